@@ -1,0 +1,374 @@
+"""Benchmark: decoupled closeness centrality on a HoMLN, one GPU per rank.
+
+One step = one pass of the whole hot path over one HoMLN:
+  CSR build of every layer -> all-sources BFS closeness of every layer (Psi) ->
+  AND aggregation + all-sources BFS closeness of the AND graph (ground truth) ->
+  top-10% CC nodes -> naive, CC1 and CC2 composition (Theta) -> accuracy of each.
+
+Workload (default): 4 Chung-Lu power-law layers (exponent 2.5, average degree 10)
+on 50,000 shared nodes with a shared edge pool of rho*m edges, rho ~ U[0.3, 0.7]
+(seeded synthetic stand-in for the paper's RMAT/PaRMAT HoMLNs).
+
+Metric: GTEPS = sum over the analysed graphs of sum_s |E(component(s))| / time
+(Graph500 convention for all-sources BFS), whole job over all ranks.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS and % HBM roofline of all-sources closeness; batched vs plain speedup"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="powerlaw50k", choices=["powerlaw50k", "ba200k", "er1k"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-sources", type=int, default=1500)
+    p.add_argument("--words", type=int, default=0, help="BFS words per node (0 = auto)")
+    p.add_argument("--alpha", type=int, default=0)
+    return p.parse_args()
+
+
+def make_workload(name: str, rank: int):
+    from paper_2207_11662_gb300 import synth
+    if name == "powerlaw50k":
+        net = synth.homln_powerlaw(n=50000, avg_deg=10.0, n_layers=4, gamma=2.5, seed=2001 + 7919 * rank)
+        desc = (f"4 Chung-Lu layers (gamma 2.5, avg deg 10), n=50000, shared pool rho={net.meta['rho']:.3f}; "
+                "per-layer + AND all-sources closeness, top-10%, naive/CC1/CC2, accuracy")
+    elif name == "ba200k":
+        net = synth.homln_ba_large(n=200000, m_attach=4, n_layers=4, seed=4001 + 7919 * rank)
+        desc = "4 BA layers (m=4), n=200000, ~50% shared edges; full hot path"
+    else:
+        net = synth.homln_small_er(seeds=(101 + rank, 102 + rank, 103 + rank))
+        desc = "3 ER layers (avg deg 8), n=1000; full hot path"
+    return net, desc
+
+
+def teps_work(n: int, layers) -> int:
+    """sum over analysed graphs of sum_s |E(comp(s))| = sum over components of n_c * m_c."""
+    import scipy.sparse as sps
+    from scipy.sparse.csgraph import connected_components
+
+    def canon(s, d):
+        s = s.astype(np.int64)
+        d = d.astype(np.int64)
+        k = s != d
+        lo, hi = np.minimum(s[k], d[k]), np.maximum(s[k], d[k])
+        return np.unique(lo * n + hi)
+
+    keys = [canon(s, d) for s, d in layers]
+    inter = keys[0]
+    for k in keys[1:]:
+        inter = np.intersect1d(inter, k, assume_unique=True)
+    total = 0
+    for k in keys + [inter]:
+        lo, hi = k // n, k % n
+        A = sps.coo_matrix((np.ones(lo.shape[0]), (lo, hi)), shape=(n, n)).tocsr()
+        nc, lab = connected_components(A, directed=False)
+        nodes = np.bincount(lab, minlength=nc).astype(np.int64)
+        edges = np.bincount(lab[lo], minlength=nc).astype(np.int64)
+        total += int(np.sum(nodes * edges))
+    return total, [int(k.shape[0]) for k in keys + [inter]]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def bfs_bytes(prof: dict) -> float:
+    """Algorithmic bytes of the BFS launches (the byte model is stated in the design doc):
+    gathered frontier words (8 B) + column indices of scanned and pushed edges (4 B) +
+    pushed words (8 B atomic OR) + the per-level vertex sweeps counted by the library."""
+    return (8.0 * prof["words_gathered"] + 4.0 * (prof["edges_scanned"] + prof["edges_pushed"]) +
+            8.0 * prof["words_pushed"] + float(prof["sweep_bytes"]))
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2207_11662_gb300 import homln as H
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    net, desc = make_workload(args.workload, rank)
+    n, L = net.n, net.n_layers
+    full = (1 << L) - 1
+    work, edge_counts = teps_work(n, net.layers)
+    tuning = {}
+    if args.words:
+        tuning["words_per_node"] = args.words
+    if args.alpha:
+        tuning["push_alpha"] = args.alpha
+    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
+    stream = torch.cuda.current_stream(dev)
+    dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(layers, host_out=False, profile=None):
+        h = H.homln_create(n, layers, stream=stream.cuda_stream)
+        try:
+            if tuning:
+                H.homln_set_tuning(h, **tuning)
+            if profile is not None:
+                H.homln_set_profiling(h, profile == "time", profile == "count")
+            if host_out:
+                F = np.empty(n, np.uint64)
+                R = np.empty(n, np.uint32)
+                cc = np.empty(n, np.float64)
+                ids = [np.empty(n, np.int32) for _ in range(4)]
+            else:
+                F = torch.empty(n, dtype=torch.int64, device=dev)
+                R = torch.empty(n, dtype=torch.int32, device=dev)
+                cc = torch.empty(n, dtype=torch.float64, device=dev)
+                ids = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
+            outs = []
+            for i in range(L):
+                H.homln_layer_closeness(h, i, F, R, cc)
+                outs.append(None)
+            m_and = H.homln_and_aggregate(h, full)
+            H.homln_and_closeness(h, full, F, R, cc)
+            cg = H.homln_topk(h, -1, full, sel, ids[0])
+            accs = []
+            for j, heur in enumerate((H.HOMLN_NAIVE, H.HOMLN_CC1, H.HOMLN_CC2)):
+                c = H.homln_compose(h, full, heur, sel, ids[j + 1])
+                accs.append(H.homln_accuracy(h, ids[j + 1], c, ids[0], cg))
+            prof = H.homln_get_profile(h) if profile is not None else None
+            return accs, prof, m_and
+        finally:
+            H.homln_destroy(h)
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(dlayers)
+    torch.cuda.synchronize()
+    # untimed instrumented pass: the algorithmic work of the BFS kernels
+    _, prof_count, m_and = step(dlayers, profile="count")
+    alg_bytes_total = bfs_bytes(prof_count)
+    alg_bytes_per_launch = alg_bytes_total / max(prof_count["bfs_launches"], 1)
+
+    # timed region (device-resident inputs)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = H.homln_kernel_launches()
+    bfs_ms, bfs_launches = 0.0, 0
+    accs = None
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)  # evict L2 between steps (512 MB > 129 MB)
+            ev[k][0].record(stream)
+            accs, prof, _ = step(dlayers, profile="time")
+            ev[k][1].record(stream)
+            bfs_ms += prof["bfs_ms"]
+            bfs_launches += prof["bfs_timed_launches"]
+        torch.cuda.synchronize()
+    launches = H.homln_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    torch.cuda.synchronize()
+
+    # end to end through the C-ABI with host buffers: pinned inputs, H2D + D2H inside the timed region
+    pinned = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory()) for s, d in net.layers]
+    h2d = sum(int(s.numel() + d.numel()) * 4 for s, d in pinned)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step([(s.numpy(), d.numpy()) for s, d in pinned], host_out=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+    d2h = (L + 1) * n * (8 + 4 + 8) + 4 * n * 4
+    e2e_t = statistics.mean(e2e_ms) / 1000.0
+
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes_per_launch / (bfs_ms / max(bfs_launches, 1) / 1000.0) / 1e9
+    result = {
+        "metric": METRIC,
+        "value": None,
+        "unit": "GTEPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max * 1000.0 / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (seeded Chung-Lu/ER/BA HoMLN, shapes of the paper's workloads)",
+        "config": {"workload": desc, "n": n, "layers": L, "undirected_edges": edge_counts,
+                   "teps_edges_per_step": work, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world} (one HoMLN per GPU)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_msbfs (persistent all-sources BFS, one launch per graph)",
+                     "algorithmic_bytes_per_launch": round(alg_bytes_per_launch),
+                     "launch_ms": round(bfs_ms / max(bfs_launches, 1), 4),
+                     "bfs_share_of_step": round(bfs_ms / sum(step_ms), 4)},
+        "e2e": {"value": round(work / e2e_t / 1e9, 3), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_t * 1000.0, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "accuracy_vs_ground_truth": {nm: {k: round(a[k], 4) for k in ("jaccard", "precision", "recall", "f1")}
+                                     for nm, a in zip(("naive", "cc1", "cc2"), accs)},
+        "bfs_profile": {k: prof_count[k] for k in ("levels", "pull_levels", "push_levels", "batches",
+                                                   "edges_scanned", "words_gathered", "edges_pushed",
+                                                   "words_pushed", "sweep_bytes", "words_per_node")},
+    }
+    result["value"] = round(work * world * args.steps / t_max / 1e9, 3)
+    return result, net
+
+
+def cpu_baseline(net, sources_per_graph: int, seed: int = 2001):
+    """The oracle as it stands: queue BFS from a seeded sample of sources on every analysed graph."""
+    from oracle import oracle as O
+    n = net.n
+    keys = [O.edge_keys(n, s, d) for s, d in net.layers]
+    graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    import scipy.sparse as sps
+    from scipy.sparse.csgraph import connected_components
+    work = 0
+    t = 0.0
+    for rp, col in graphs:
+        src = np.sort(rng.choice(n, min(sources_per_graph, n), replace=False)).astype(np.int32)
+        A = sps.csr_matrix((np.ones(col.shape[0]), col, rp), shape=(n, n))
+        nc, lab = connected_components(A, directed=False)
+        deg = np.diff(rp)
+        m_comp = np.bincount(lab, weights=deg, minlength=nc) / 2
+        work += int(np.sum(m_comp[lab[src]]))
+        t0 = time.perf_counter()
+        O.farness_reach(n, rp, col, sources=src, threads=threads)
+        t += time.perf_counter() - t0
+    return {"value": round(work / t / 1e9, 4), "unit": "GTEPS", "cores": threads, "kind": "oracle",
+            "sample": f"queue BFS from {sources_per_graph} seeded sources on each of the {len(graphs)} graphs "
+                      f"(4 layers + AND), {t:.1f} s of CPU work, OpenMP over sources"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    dist = None
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        net, desc = make_workload(args.workload, 0)
+        for _ in range(args.warmup):
+            cpu_baseline(net, max(50, args.cpu_sample_sources // 10))
+        vals = [cpu_baseline(net, args.cpu_sample_sources, seed=2001 + k) for k in range(args.steps)]
+        v = statistics.mean(x["value"] for x in vals)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GTEPS",
+                          "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                          "config": {"workload": desc},
+                          "cpu_baseline": dict(vals[-1], value=round(v, 4)),
+                          "e2e": {"value": round(v, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", init_method="env://")
+        dist = tdist
+    result, net = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)
+        print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * homln.h -- C-ABI of the GB300 library for decoupled closeness centrality on
+ * homogeneous multilayer networks (HoMLNs).
+ *
+ * Method: Pavel, Roy, Santra, Chakravarthy, "Closeness Centrality Detection in
+ * Homogeneous Multilayer Networks" (arXiv 2207.11662).
+ *   Problem statement (Section 1): given layers G_1(V,E_1) ... G_l(V,E_l) over one
+ *   vertex set, find the closeness-centrality (CC) nodes of the Boolean-AND
+ *   aggregate of any r <= l layers from partial results of each layer
+ *   (analysis step Psi, composition step Theta).
+ *
+ * Conventions used by every call
+ *   - Graphs are undirected and unweighted. Node ids are int32 in [0, n).
+ *     Self loops and repeated edges in the input are accepted and dropped
+ *     (simple-graph semantics, Section 4).
+ *   - All GPU work runs on the CUDA stream given to homln_create, on the device
+ *     that was current at homln_create.
+ *   - Output pointers may be host memory (pageable or pinned) or device memory;
+ *     the library asks the CUDA runtime which it is. A call that writes any host
+ *     output returns after the data is there (it synchronises the stream). A call
+ *     whose outputs are all device memory only enqueues work and returns; errors
+ *     raised by that work on the device surface at the next synchronising call or
+ *     at homln_sync.
+ *   - Every call returns a homln_status. No C++ exception crosses this boundary.
+ *     On error the outputs are left untouched unless stated otherwise, and
+ *     homln_last_error() returns a message for the calling thread.
+ *   - The caller owns every buffer it passes. The handle owns all device memory
+ *     it allocates (CSRs, AND graphs, BFS state, cached results) and frees it
+ *     in homln_destroy.
+ *   - A handle is not thread safe: one thread at a time may call into it.
+ */
+#ifndef HOMLN_H
+#define HOMLN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HOMLN_API __attribute__((visibility("default")))
+#else
+#define HOMLN_API
+#endif
+
+/* Opaque handle: one HoMLN resident on one GPU. */
+typedef struct homln_s *homln_t;
+
+#define HOMLN_MAX_LAYERS 64
+#define HOMLN_MAX_NODES 1048576 /* 2^20: (n-1)*farness stays below 2^60 */
+
+typedef enum homln_status {
+    HOMLN_OK = 0,
+    HOMLN_EINVAL = 1,   /* bad argument: null handle, id out of range, empty mask, n out of range ... */
+    HOMLN_ENOMEM = 2,   /* the allocator returned NULL */
+    HOMLN_ECUDA = 3,    /* a CUDA runtime call failed (message in homln_last_error) */
+    HOMLN_ERANGE = 4,   /* an output capacity is too small, or a value left its exact range */
+    HOMLN_ETIMEOUT = 5, /* a bounded device-side wait gave up (the kernel returned early) */
+    HOMLN_EBUSY = 6     /* the handle is in use by a batched launch */
+} homln_status;
+
+/* homln_create flags */
+#define HOMLN_PTR_HOST 0u   /* edge arrays are host memory */
+#define HOMLN_PTR_DEVICE 1u /* edge arrays are device memory of the current device */
+
+/* Composition heuristics: naive (Section 4), CC1 (Section 5.1), CC2 (Section 5.2, Algorithm 1). */
+typedef enum homln_heuristic { HOMLN_NAIVE = 0, HOMLN_CC1 = 1, HOMLN_CC2 = 2 } homln_heuristic;
+
+/* CC-node selection rule.
+ *   TOPK_PERCENT: the k = ceil(percent * n / 100) highest scores (double arithmetic).
+ *   TOPK_COUNT:   the k highest scores (k clamped to [0, n]).
+ *   GE_MEAN:      every node whose score is >= the mean score ("same or above
+ *                 average", Section 4), decided exactly on the float64 scores.
+ *   GT_MEAN:      strictly above the mean.
+ * Ranking: score descending, equal scores by ascending node id.
+ * cc1_overlap is CC1's "significant overlap" threshold theta (Section 5.1 leaves
+ * it undefined): a common CC node u is kept iff |AND of C_i(u)| >= theta*|OR of C_i(u)|
+ * and the union is non-empty. */
+typedef enum homln_select_mode {
+    HOMLN_TOPK_PERCENT = 0,
+    HOMLN_TOPK_COUNT = 1,
+    HOMLN_GE_MEAN = 2,
+    HOMLN_GT_MEAN = 3
+} homln_select_mode;
+
+typedef struct homln_select {
+    int32_t mode;       /* homln_select_mode */
+    int32_t reserved;   /* must be 0 */
+    double percent;     /* TOPK_PERCENT */
+    int64_t k;          /* TOPK_COUNT */
+    double cc1_overlap; /* CC1 theta in [0, 1] */
+} homln_select;
+
+/* Device-memory allocator. alloc returns device memory usable on `stream`
+ * (or NULL on failure); free releases it in stream order. NULL for the whole
+ * struct selects cudaMallocAsync/cudaFreeAsync. The library calls it from the
+ * thread that called into the library. */
+typedef struct homln_allocator {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} homln_allocator;
+
+/* Accuracy of an estimated CC-node set against ground truth (Section 5,
+ * Section 6.1): the paper's "accuracy" is the Jaccard coefficient.
+ *   jaccard = tp/(tp+fp+fn) (1 when all three are 0), precision = tp/(tp+fp),
+ *   recall = tp/(tp+fn), f1 = 2tp/(2tp+fp+fn) (each 0 when its denominator is 0). */
+typedef struct homln_accuracy_t {
+    int64_t tp, fp, fn;
+    double jaccard, precision, recall, f1;
+} homln_accuracy_t;
+
+/* Tuning knobs of the multi-source BFS; zero fields take the built-in defaults. */
+typedef struct homln_tuning {
+    int32_t words_per_node;  /* W: 64*W sources per BFS batch; 1, 2, 4, 8, 16 or 32 (0 = auto) */
+    int32_t push_alpha;      /* go top-down when alpha * frontier_edges < unfinished_edges (0 = default 8) */
+    int32_t threads;         /* threads per block of the persistent BFS (0 = 512) */
+    int32_t blocks_per_sm;   /* resident blocks per SM (0 = as many as fit) */
+    int32_t relabel;         /* 1 = degree-descending relabelling of each graph before BFS, 0 = off, -1 = default */
+    int32_t reserved[3];
+} homln_tuning;
+
+/* Create a handle: copy the layers to the device and build one CSR per layer.
+ *   n_nodes      number of shared nodes n, 1 <= n <= HOMLN_MAX_NODES (Section 1: |V| is shared).
+ *   n_layers     number of layers l, 1 <= l <= HOMLN_MAX_LAYERS.
+ *   edge_counts  host array[n_layers]: edges in layer i (>= 0).
+ *   src, dst     host arrays[n_layers] of pointers; layer i's edges are
+ *                (src[i][e], dst[i][e]), e < edge_counts[i], int32, host or device
+ *                memory according to `flags`.
+ *   flags        HOMLN_PTR_HOST or HOMLN_PTR_DEVICE.
+ *   alloc        device allocator or NULL (see homln_allocator).
+ *   stream       cudaStream_t to run on (NULL = the legacy default stream).
+ *   out          receives the handle.
+ * Synchronous: returns after the CSRs are built and every id has been checked.
+ * Errors: EINVAL (n, l, counts, null pointers, an id outside [0, n)), ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge_counts,
+                          const int32_t *const *src, const int32_t *const *dst, uint32_t flags,
+                          const homln_allocator *alloc, void *stream, homln_t *out);
+
+/* Release everything the handle owns (stream-ordered frees, then a stream synchronise). NULL is a no-op. */
+HOMLN_API homln_status homln_destroy(homln_t h);
+
+/* Set the BFS tuning of a handle (copied). NULL restores defaults. */
+HOMLN_API homln_status homln_set_tuning(homln_t h, const homln_tuning *t);
+
+/* Psi for one layer (Section 3: each layer analysed once; Section 4: BFS from every vertex).
+ * Runs the all-sources BFS once per layer and caches the result in the handle.
+ *   farness[n] (uint64): F(v) = sum of hop distances from v to the vertices it reaches.
+ *   reach[n]   (uint32): R(v) = vertices reachable from v, v excluded.
+ *   cc[n]      (double): Wasserman-Faust closeness R^2 / ((n-1) F), 0 when F = 0; on a
+ *              connected layer this is Eq. 1, (n-1)/F. One correctly rounded division.
+ * Any output may be NULL. Errors: EINVAL (layer out of range), ENOMEM, ECUDA, ETIMEOUT. */
+HOMLN_API homln_status homln_layer_closeness(homln_t h, int32_t layer, uint64_t *farness, uint32_t *reach, double *cc);
+
+/* Boolean AND aggregation of the layers in `layer_mask` (Section 3.1, Section 4 ground truth):
+ * an edge is kept iff it is present in every selected layer. The AND graph is built
+ * once per mask and cached. Edges are written as pairs u < v in ascending (u, v) order.
+ *   capacity       entries available in and_src/and_dst (ignored when both are NULL).
+ *   and_src/dst    int32 outputs (host or device), or NULL to query the count only.
+ *   and_edge_count host int64 output: number of undirected AND edges (always written on OK/ERANGE).
+ * Errors: EINVAL (empty mask or a bit >= n_layers), ERANGE (capacity < count), ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity, int32_t *and_src,
+                                 int32_t *and_dst, int64_t *and_edge_count);
+
+/* Ground truth closeness: all-sources BFS on the AND graph of `layer_mask` (Section 4).
+ * Same outputs and rules as homln_layer_closeness. */
+HOMLN_API homln_status homln_and_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach, double *cc);
+
+/* CC nodes of one graph: which = layer id, or -1 for the AND graph of layer_mask (then the
+ * ground truth). Scores are the closeness values of homln_*_closeness; the selection rule
+ * is `sel`. nodes_out (capacity n, host or device) receives the ids in rank order;
+ * count_out (host) the number written.
+ * Errors: EINVAL (which/mask/sel), ENOMEM, ECUDA, ETIMEOUT. */
+HOMLN_API homln_status homln_topk(homln_t h, int32_t which, uint64_t layer_mask, const homln_select *sel,
+                        int32_t *nodes_out, int32_t *count_out);
+
+/* Theta: estimated CC nodes of the AND aggregate of `layer_mask` from per-layer partial results.
+ *   HOMLN_NAIVE  intersection of the layers' CC-node sets (Section 4).
+ *   HOMLN_CC1    Section 5.1: Eq. 2 ratio sumDist_i(u)/min_j deg_j(u), Eq. 3 average = max of the
+ *                layers' exact mean ratios, central neighbours (ratio < average), overlap test.
+ *   HOMLN_CC2    Section 5.2, Algorithm 1: estSumDist(u) = max_i sumDist_i(u), scored with Eq. 1
+ *                as (n-1)/estSumDist(u), then `sel`.
+ * sumDist charges n for each unreachable node (Section 5.1). With r > 2 layers the pairwise
+ * rules apply across all r (intersection, max, min). Layer CC-node sets use `sel`.
+ * nodes_out (capacity n, host or device) receives the ids in ascending order; count_out (host)
+ * the number written. Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+HOMLN_API homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, const homln_select *sel,
+                           int32_t *nodes_out, int32_t *count_out);
+
+/* Accuracy of `pred` against `truth` (node-id lists, host or device, duplicates ignored),
+ * over the handle's node set. Errors: EINVAL (negative length, id outside [0, n)), ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, const int32_t *truth,
+                            int32_t n_truth, homln_accuracy_t *out);
+
+/* Measurement support (no counterpart in the paper; used by the benchmark).
+ * homln_set_profiling: timing != 0 records CUDA events on the handle's stream right
+ * around every BFS kernel launch; instrument != 0 runs the BFS kernels in a
+ * counting variant (levels, edges scanned, words gathered) -- slower, for an
+ * untimed pass that measures the algorithmic work. Both apply to later analyses.
+ * homln_get_profile synchronises the stream and sums what was recorded since
+ * the last homln_reset_profile. */
+typedef struct homln_profile_t {
+    int64_t bfs_launches;       /* all-sources BFS kernels launched */
+    int64_t bfs_timed_launches; /* of which event-timed */
+    double bfs_ms;              /* summed device time of the timed launches */
+    int64_t levels, pull_levels, push_levels, batches; /* instrumented runs only */
+    int64_t edges_scanned;      /* bottom-up neighbour visits (per vertex) */
+    int64_t words_gathered;     /* 8-byte frontier words read by bottom-up levels */
+    int64_t edges_pushed;       /* top-down neighbour visits */
+    int64_t words_pushed;       /* 8-byte atomic ORs of top-down levels */
+    int64_t sweep_bytes;        /* bytes of the per-level vertex sweeps (seen, next, rowptr, accumulator) */
+    int32_t words_per_node;     /* W of the last instrumented launch */
+    int32_t reserved;
+} homln_profile_t;
+
+HOMLN_API homln_status homln_set_profiling(homln_t h, int32_t timing, int32_t instrument);
+HOMLN_API homln_status homln_get_profile(homln_t h, homln_profile_t *out);
+HOMLN_API homln_status homln_reset_profile(homln_t h);
+/* Number of kernels this library has launched in the process so far. */
+HOMLN_API int64_t homln_kernel_launches(void);
+
+/* Wait for all work queued by the handle and report any device-side error it raised. */
+HOMLN_API homln_status homln_sync(homln_t h);
+
+/* Message describing the last error on the calling thread ("" if none). */
+HOMLN_API const char *homln_last_error(void);
+
+/* Library version string. */
+HOMLN_API const char *homln_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOMLN_H */

@@ -1,0 +1,555 @@
+// The C-ABI (include/homln.h): handle management, argument checking, host/device
+// output placement and the Psi / Theta call sequence of the decoupled method.
+//
+// Psi (Section 3): each layer is analysed once -- all-sources BFS closeness --
+// and its partial results (F, R, closeness, sumDist, degree) are cached in the
+// handle. Theta (Section 4, Section 5): compositions read only those partial
+// results (plus the layer CSRs for CC1). Ground truth (Section 4): the AND
+// aggregate of the selected layers, analysed the same way.
+#include "common.cuh"
+
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+
+namespace homln {
+
+std::atomic<long long> g_kernel_launches{0};
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void fail(homln_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{HOMLN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+    }
+}
+
+void *Alloc::get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (a.alloc) return a.alloc(a.ctx, bytes, (void *)stream);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Alloc::put(void *p, size_t bytes) {
+    if (!p) return;
+    if (a.free) a.free(a.ctx, p, bytes ? bytes : 16, (void *)stream);
+    else cudaFreeAsync(p, stream);
+}
+
+// Partial results of one analysed graph (a layer or an AND aggregate).
+struct GraphState {
+    Csr csr;
+    bool analysed = false;
+    DBuf<uint64_t> F;
+    DBuf<uint32_t> R;
+    DBuf<double> cc;
+    DBuf<uint64_t> sumdist;
+    DBuf<int32_t> deg;
+};
+
+}  // namespace homln
+
+using namespace homln;
+
+struct homln_s {
+    Alloc al;  // declared first: destroyed last, after every buffer that uses it
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n = 0, L = 0;
+    BfsTuning tuning;
+    DBuf<int32_t> err;
+    std::vector<std::unique_ptr<GraphState>> layers;
+    std::map<uint64_t, std::unique_ptr<GraphState>> ands;
+    bool profiling = false;
+    bool instrument = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    long long bfs_launches = 0;
+    BfsStats stats;
+    ~homln_s() {
+        for (auto &e : events) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    }
+};
+
+namespace {
+
+#define API_BEGIN try {
+#define API_END                                           \
+    }                                                     \
+    catch (const homln::Error &e) {                       \
+        set_error(e.msg);                                 \
+        return e.code;                                    \
+    }                                                     \
+    catch (const std::bad_alloc &) {                      \
+        set_error("host allocation failed");              \
+        return HOMLN_ENOMEM;                              \
+    }                                                     \
+    catch (...) {                                         \
+        set_error("unexpected internal error");           \
+        return HOMLN_ECUDA;                               \
+    }                                                     \
+    set_error("");                                        \
+    return HOMLN_OK;
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void use_device(homln_t h) { HCUDA(cudaSetDevice(h->device)); }
+
+// Map a device-side error word to a status (and clear it).
+void check_device_error(homln_t h) {
+    int32_t e = 0;
+    HCUDA(cudaMemcpyAsync(&e, h->err.p, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
+    HCUDA(cudaStreamSynchronize(h->stream));
+    if (e == DEV_OK) return;
+    HCUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->stream));
+    switch (e) {
+    case DEV_BAD_ID: fail(HOMLN_EINVAL, "node id outside [0, n)");
+    case DEV_TIMEOUT: fail(HOMLN_ETIMEOUT, "a bounded device wait gave up");
+    case DEV_RANGE: fail(HOMLN_ERANGE, "a value left the exact fixed-point range");
+    default: fail(HOMLN_ECUDA, "unknown device error");
+    }
+}
+
+// Copy `bytes` from device memory to `dst` (host or device). Returns true if dst is host memory.
+bool put_out(homln_t h, void *dst, const void *dsrc, size_t bytes) {
+    if (!dst || bytes == 0) return false;
+    bool dev = is_device_ptr(dst);
+    HCUDA(cudaMemcpyAsync(dst, dsrc, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    return !dev;
+}
+
+// A device view of a caller buffer: the buffer itself if it is device memory, else a staging copy.
+template <typename T>
+struct DevIn {
+    const T *p = nullptr;
+    DBuf<T> tmp;
+    void from(homln_t h, const T *src, size_t count) {
+        if (count == 0 || is_device_ptr(src)) {
+            p = src;
+            return;
+        }
+        if (!tmp.alloc(&h->al, count)) fail(HOMLN_ENOMEM, "staging copy");
+        HCUDA(cudaMemcpyAsync(tmp.p, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+        p = tmp.p;
+    }
+};
+
+// A device target for an output: the caller's buffer if device memory, else scratch to copy from.
+template <typename T>
+struct DevOut {
+    T *p = nullptr;
+    T *user = nullptr;
+    size_t count = 0;
+    DBuf<T> tmp;
+    void to(homln_t h, T *dst, size_t cnt) {
+        user = dst;
+        count = cnt;
+        if (dst && is_device_ptr(dst)) {
+            p = dst;
+            return;
+        }
+        if (!tmp.alloc(&h->al, cnt > 0 ? cnt : 1)) fail(HOMLN_ENOMEM, "output scratch");
+        p = tmp.p;
+    }
+    bool finish(homln_t h, size_t written) {
+        if (!user || p == user || written == 0) return false;
+        HCUDA(cudaMemcpyAsync(user, p, written * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+        return true;
+    }
+};
+
+void analyse(homln_t h, GraphState &g) {
+    if (g.analysed) return;
+    const int32_t n = h->n;
+    if (!g.F.alloc(&h->al, n) || !g.R.alloc(&h->al, n) || !g.cc.alloc(&h->al, n) || !g.sumdist.alloc(&h->al, n) ||
+        !g.deg.alloc(&h->al, n))
+        fail(HOMLN_ENOMEM, "closeness outputs");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profiling) {
+        HCUDA(cudaEventCreate(&e0));
+        HCUDA(cudaEventCreate(&e1));
+        h->events.push_back({e0, e1});
+    }
+    BfsStats st;
+    msbfs_all_sources(g.csr, g.F.p, g.R.p, h->tuning, h->err.p, &h->al, h->stream, h->instrument ? &st : nullptr,
+                      nullptr, e0, e1);
+    if (h->instrument) {
+        h->stats.levels += st.levels;
+        h->stats.pull_levels += st.pull_levels;
+        h->stats.push_levels += st.push_levels;
+        h->stats.group_edges += st.group_edges;
+        h->stats.lane_words += st.lane_words;
+        h->stats.push_edges += st.push_edges;
+        h->stats.batches += st.batches;
+        h->stats.push_words += st.push_words;
+        h->stats.sweep_bytes += st.sweep_bytes;
+        h->stats.words_per_node = st.words_per_node;
+    }
+    h->bfs_launches += 1;
+    closeness_finalize(n, g.csr.rowptr.p, g.F.p, g.R.p, g.cc.p, g.sumdist.p, g.deg.p, h->stream);
+    g.analysed = true;
+}
+
+std::vector<int> mask_layers(homln_t h, uint64_t mask) {
+    if (mask == 0) fail(HOMLN_EINVAL, "empty layer mask");
+    if (h->L < 64 && (mask >> h->L) != 0) fail(HOMLN_EINVAL, "layer mask names a layer that does not exist");
+    std::vector<int> out;
+    for (int i = 0; i < h->L; ++i)
+        if ((mask >> i) & 1ull) out.push_back(i);
+    return out;
+}
+
+GraphState &and_graph(homln_t h, uint64_t mask) {
+    std::vector<int> ids = mask_layers(h, mask);
+    auto it = h->ands.find(mask);
+    if (it != h->ands.end()) return *it->second;
+    auto g = std::make_unique<GraphState>();
+    if (ids.size() == 1) {
+        const Csr &src = h->layers[ids[0]]->csr;
+        g->csr.n = src.n;
+        g->csr.nnz = src.nnz;
+        if (!g->csr.rowptr.alloc(&h->al, (size_t)h->n + 1) || !g->csr.col.alloc(&h->al, src.nnz > 0 ? src.nnz : 1))
+            fail(HOMLN_ENOMEM, "and graph");
+        HCUDA(cudaMemcpyAsync(g->csr.rowptr.p, src.rowptr.p, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToDevice,
+                              h->stream));
+        if (src.nnz > 0)
+            HCUDA(cudaMemcpyAsync(g->csr.col.p, src.col.p, sizeof(int32_t) * src.nnz, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+    } else {
+        std::vector<const Csr *> ls;
+        for (int i : ids) ls.push_back(&h->layers[i]->csr);
+        and_intersect(h->n, ls, g->csr, &h->al, h->stream);
+    }
+    GraphState &ref = *g;
+    h->ands.emplace(mask, std::move(g));
+    return ref;
+}
+
+void check_select(const homln_select *sel) {
+    if (!sel) fail(HOMLN_EINVAL, "selection is NULL");
+    if (sel->reserved != 0) fail(HOMLN_EINVAL, "homln_select.reserved must be 0");
+    if (sel->mode < HOMLN_TOPK_PERCENT || sel->mode > HOMLN_GT_MEAN) fail(HOMLN_EINVAL, "unknown selection mode");
+    if (sel->mode == HOMLN_TOPK_PERCENT && !(sel->percent >= 0.0 && sel->percent <= 100.0))
+        fail(HOMLN_EINVAL, "percent must be in [0, 100]");
+    if (sel->mode == HOMLN_TOPK_COUNT && sel->k < 0) fail(HOMLN_EINVAL, "k must be >= 0");
+    if (!(sel->cc1_overlap >= 0.0 && sel->cc1_overlap <= 1.0)) fail(HOMLN_EINVAL, "cc1_overlap must be in [0, 1]");
+}
+
+void write_closeness(homln_t h, GraphState &g, uint64_t *F, uint32_t *R, double *cc) {
+    bool host = false;
+    host |= put_out(h, F, g.F.p, sizeof(uint64_t) * h->n);
+    host |= put_out(h, R, g.R.p, sizeof(uint32_t) * h->n);
+    host |= put_out(h, cc, g.cc.p, sizeof(double) * h->n);
+    if (host) check_device_error(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *homln_last_error(void) { return g_last_error.c_str(); }
+
+const char *homln_version(void) { return "homln-gb300 0.1 (sm_103a)"; }
+
+homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge_counts, const int32_t *const *src,
+                          const int32_t *const *dst, uint32_t flags, const homln_allocator *alloc, void *stream,
+                          homln_t *out) {
+    API_BEGIN
+    if (!out) fail(HOMLN_EINVAL, "out is NULL");
+    if (n_nodes < 1 || n_nodes > HOMLN_MAX_NODES) fail(HOMLN_EINVAL, "n_nodes must be in [1, 2^20]");
+    if (n_layers < 1 || n_layers > HOMLN_MAX_LAYERS) fail(HOMLN_EINVAL, "n_layers must be in [1, 64]");
+    if (!edge_counts || !src || !dst) fail(HOMLN_EINVAL, "edge_counts, src and dst must not be NULL");
+    if (flags > HOMLN_PTR_DEVICE) fail(HOMLN_EINVAL, "unknown flags");
+    for (int i = 0; i < n_layers; ++i) {
+        if (edge_counts[i] < 0 || edge_counts[i] > (int64_t(1) << 31)) fail(HOMLN_EINVAL, "edge count out of range");
+        if (edge_counts[i] > 0 && (!src[i] || !dst[i])) fail(HOMLN_EINVAL, "edge array is NULL");
+    }
+    if (alloc && (!alloc->alloc || !alloc->free)) fail(HOMLN_EINVAL, "allocator needs both alloc and free");
+    auto h = std::make_unique<homln_s>();
+    HCUDA(cudaGetDevice(&h->device));
+    h->stream = (cudaStream_t)stream;
+    h->al.stream = h->stream;
+    if (alloc) h->al.a = *alloc;
+    else std::memset(&h->al.a, 0, sizeof(h->al.a));
+    h->n = n_nodes;
+    h->L = n_layers;
+    if (!h->err.alloc(&h->al, 1)) fail(HOMLN_ENOMEM, "error word");
+    HCUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->stream));
+    for (int i = 0; i < n_layers; ++i) {
+        auto g = std::make_unique<GraphState>();
+        const int64_t m = edge_counts[i];
+        DBuf<int32_t> ds, dd;
+        const int32_t *ps = src[i], *pd = dst[i];
+        if (m > 0 && flags == HOMLN_PTR_HOST) {
+            if (!ds.alloc(&h->al, m) || !dd.alloc(&h->al, m)) fail(HOMLN_ENOMEM, "edge staging");
+            HCUDA(cudaMemcpyAsync(ds.p, ps, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+            HCUDA(cudaMemcpyAsync(dd.p, pd, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+            ps = ds.p;
+            pd = dd.p;
+        }
+        build_csr(n_nodes, ps, pd, m, g->csr, h->err.p, &h->al, h->stream);
+        h->layers.push_back(std::move(g));
+    }
+    check_device_error(h.get());
+    *out = h.release();
+    API_END
+}
+
+homln_status homln_destroy(homln_t h) {
+    if (!h) return HOMLN_OK;
+    API_BEGIN
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    delete h;
+    HCUDA(cudaStreamSynchronize(s));
+    API_END
+}
+
+homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    BfsTuning bt;
+    if (t) {
+        if (t->words_per_node) {
+            int W = t->words_per_node;
+            if (W != 1 && W != 2 && W != 4 && W != 8 && W != 16 && W != 32)
+                fail(HOMLN_EINVAL, "words_per_node must be 1, 2, 4, 8, 16 or 32");
+            bt.W = W;
+        }
+        if (t->push_alpha < 0) fail(HOMLN_EINVAL, "push_alpha must be >= 0");
+        if (t->push_alpha) bt.push_alpha = t->push_alpha;
+        if (t->threads) {
+            if (t->threads < 64 || t->threads > 512 || t->threads % 32) fail(HOMLN_EINVAL, "threads must be 64..512, x32");
+            bt.threads = t->threads;
+        }
+        if (t->blocks_per_sm < 0) fail(HOMLN_EINVAL, "blocks_per_sm must be >= 0");
+        bt.blocks_per_sm = t->blocks_per_sm;
+        if (t->relabel >= 0) bt.relabel = t->relabel ? 1 : 0;
+    }
+    h->tuning = bt;
+    API_END
+}
+
+homln_status homln_layer_closeness(homln_t h, int32_t layer, uint64_t *farness, uint32_t *reach, double *cc) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (layer < 0 || layer >= h->L) fail(HOMLN_EINVAL, "layer out of range");
+    use_device(h);
+    GraphState &g = *h->layers[layer];
+    analyse(h, g);
+    write_closeness(h, g, farness, reach, cc);
+    API_END
+}
+
+homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity, int32_t *and_src, int32_t *and_dst,
+                                 int64_t *and_edge_count) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!and_edge_count) fail(HOMLN_EINVAL, "and_edge_count is NULL");
+    if ((and_src == nullptr) != (and_dst == nullptr)) fail(HOMLN_EINVAL, "and_src and and_dst must both be given");
+    use_device(h);
+    GraphState &g = and_graph(h, layer_mask);
+    const int64_t m = g.csr.nnz / 2;
+    if (and_src) {
+        if (capacity < m) {
+            *and_edge_count = m;
+            fail(HOMLN_ERANGE, "capacity smaller than the AND edge count");
+        }
+        DevOut<int32_t> os, od;
+        os.to(h, and_src, m);
+        od.to(h, and_dst, m);
+        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream);
+        bool host = os.finish(h, m);
+        host |= od.finish(h, m);
+        if (host) HCUDA(cudaStreamSynchronize(h->stream));
+    }
+    *and_edge_count = m;
+    API_END
+}
+
+homln_status homln_and_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach, double *cc) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    use_device(h);
+    GraphState &g = and_graph(h, layer_mask);
+    analyse(h, g);
+    write_closeness(h, g, farness, reach, cc);
+    API_END
+}
+
+homln_status homln_topk(homln_t h, int32_t which, uint64_t layer_mask, const homln_select *sel, int32_t *nodes_out,
+                        int32_t *count_out) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    check_select(sel);
+    if (!count_out) fail(HOMLN_EINVAL, "count_out is NULL");
+    if (which < -1 || which >= h->L) fail(HOMLN_EINVAL, "which must be -1 or a layer id");
+    use_device(h);
+    GraphState &g = which >= 0 ? *h->layers[which] : and_graph(h, layer_mask);
+    analyse(h, g);
+    DevOut<int32_t> o;
+    o.to(h, nodes_out, h->n);
+    int32_t c = select_nodes(h->n, g.cc.p, *sel, o.p, nullptr, h->err.p, &h->al, h->stream);
+    o.finish(h, c);
+    check_device_error(h);
+    *count_out = c;
+    API_END
+}
+
+homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, const homln_select *sel,
+                           int32_t *nodes_out, int32_t *count_out) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    check_select(sel);
+    if (!count_out) fail(HOMLN_EINVAL, "count_out is NULL");
+    if (heuristic < HOMLN_NAIVE || heuristic > HOMLN_CC2) fail(HOMLN_EINVAL, "unknown heuristic");
+    use_device(h);
+    std::vector<int> ids = mask_layers(h, layer_mask);
+    for (int i : ids) analyse(h, *h->layers[i]);
+    const int32_t n = h->n;
+    const int32_t nw = (int32_t)ceil_div(n, 32);
+    DevOut<int32_t> o;
+    o.to(h, nodes_out, n);
+    int32_t c = 0;
+    if (heuristic == HOMLN_CC2) {
+        std::vector<const uint64_t *> sd;
+        for (int i : ids) sd.push_back(h->layers[i]->sumdist.p);
+        DBuf<double> scores;
+        DBuf<int32_t> ranked;
+        DBuf<uint32_t> bits;
+        if (!scores.alloc(&h->al, n) || !ranked.alloc(&h->al, n) || !bits.alloc(&h->al, nw))
+            fail(HOMLN_ENOMEM, "cc2 scratch");
+        cc2_scores(n, sd, scores.p, &h->al, h->stream);
+        select_nodes(n, scores.p, *sel, ranked.p, bits.p, h->err.p, &h->al, h->stream);
+        c = bits_to_sorted_ids(n, bits.p, o.p, &h->al, h->stream);
+    } else {
+        // CC-node sets of the layers, intersected (naive), then CC1's refinement
+        DBuf<uint32_t> common, tmp;
+        DBuf<int32_t> ranked;
+        if (!common.alloc(&h->al, nw) || !tmp.alloc(&h->al, nw) || !ranked.alloc(&h->al, n))
+            fail(HOMLN_ENOMEM, "compose scratch");
+        for (size_t k = 0; k < ids.size(); ++k) {
+            GraphState &g = *h->layers[ids[k]];
+            select_nodes(n, g.cc.p, *sel, ranked.p, k == 0 ? common.p : tmp.p, h->err.p, &h->al, h->stream);
+            if (k > 0) bits_and(nw, common.p, tmp.p, h->stream);
+        }
+        if (heuristic == HOMLN_NAIVE) {
+            c = bits_to_sorted_ids(n, common.p, o.p, &h->al, h->stream);
+        } else {
+            std::vector<const Csr *> csrs;
+            std::vector<const uint64_t *> sd;
+            std::vector<const int32_t *> dg;
+            for (int i : ids) {
+                csrs.push_back(&h->layers[i]->csr);
+                sd.push_back(h->layers[i]->sumdist.p);
+                dg.push_back(h->layers[i]->deg.p);
+            }
+            c = cc1_compose(n, csrs, sd, dg, common.p, sel->cc1_overlap, o.p, h->err.p, &h->al, h->stream);
+        }
+    }
+    o.finish(h, c);
+    check_device_error(h);
+    *count_out = c;
+    API_END
+}
+
+homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, const int32_t *truth, int32_t n_truth,
+                            homln_accuracy_t *out) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!out) fail(HOMLN_EINVAL, "out is NULL");
+    if (n_pred < 0 || n_truth < 0) fail(HOMLN_EINVAL, "negative list length");
+    if ((n_pred > 0 && !pred) || (n_truth > 0 && !truth)) fail(HOMLN_EINVAL, "list is NULL");
+    use_device(h);
+    DevIn<int32_t> p, t;
+    p.from(h, pred, n_pred);
+    t.from(h, truth, n_truth);
+    homln_accuracy_t r;
+    accuracy_counts(h->n, p.p, n_pred, t.p, n_truth, &r, h->err.p, &h->al, h->stream);
+    check_device_error(h);
+    *out = r;
+    API_END
+}
+
+homln_status homln_sync(homln_t h) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    use_device(h);
+    HCUDA(cudaStreamSynchronize(h->stream));
+    check_device_error(h);
+    API_END
+}
+
+homln_status homln_set_profiling(homln_t h, int32_t timing, int32_t instrument) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    h->profiling = timing != 0;
+    h->instrument = instrument != 0;
+    API_END
+}
+
+homln_status homln_get_profile(homln_t h, homln_profile_t *out) {
+    API_BEGIN
+    if (!h || !out) fail(HOMLN_EINVAL, "null argument");
+    use_device(h);
+    HCUDA(cudaStreamSynchronize(h->stream));
+    double ms = 0.0;
+    for (auto &e : h->events) {
+        float t = 0.f;
+        HCUDA(cudaEventElapsedTime(&t, e.first, e.second));
+        ms += t;
+    }
+    out->bfs_launches = h->bfs_launches;
+    out->bfs_timed_launches = (int64_t)h->events.size();
+    out->bfs_ms = ms;
+    out->levels = (int64_t)h->stats.levels;
+    out->pull_levels = (int64_t)h->stats.pull_levels;
+    out->push_levels = (int64_t)h->stats.push_levels;
+    out->batches = (int64_t)h->stats.batches;
+    out->edges_scanned = (int64_t)h->stats.group_edges;
+    out->words_gathered = (int64_t)h->stats.lane_words;
+    out->edges_pushed = (int64_t)h->stats.push_edges;
+    out->words_pushed = (int64_t)h->stats.push_words;
+    out->sweep_bytes = (int64_t)h->stats.sweep_bytes;
+    out->words_per_node = h->stats.words_per_node;
+    out->reserved = 0;
+    API_END
+}
+
+homln_status homln_reset_profile(homln_t h) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    for (auto &e : h->events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    h->events.clear();
+    h->bfs_launches = 0;
+    h->stats = BfsStats{};
+    API_END
+}
+
+int64_t homln_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+}  // extern "C"

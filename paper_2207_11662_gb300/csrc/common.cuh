@@ -1,0 +1,247 @@
+// Shared device helpers and host-side plumbing of the homln library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/homln.h"
+
+namespace homln {
+
+// ---------------------------------------------------------------------------
+// Device-side error word. Kernels never trap: they record a code and return.
+// ---------------------------------------------------------------------------
+enum DevErr : int32_t {
+    DEV_OK = 0,
+    DEV_BAD_ID = 1,       // an edge endpoint outside [0, n)
+    DEV_TIMEOUT = 2,      // a bounded grid barrier gave up
+    DEV_RANGE = 3,        // an exact fixed-point value left its range
+};
+
+__device__ __forceinline__ void dev_fail(int32_t *err, int32_t code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier state: arrival counter, generation and the error word.
+struct GridBarrier {
+    uint32_t *count;
+    uint32_t *gen;
+    int32_t *err;
+};
+
+// Bounded grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Every block's thread 0 arrives once; the last arrival bumps the generation.
+// A waiter gives up after `limit_ns` of wall time, records DEV_TIMEOUT and the
+// caller returns. Returns false when the kernel must stop (timeout or error).
+__device__ __forceinline__ bool grid_sync(const GridBarrier &b, uint64_t limit_ns = 2000000000ull) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint32_t g = ld_acquire_u32(b.gen);
+        __threadfence();
+        uint32_t arrived = atomicAdd(b.count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *b.count = 0;
+            __threadfence();
+            st_release_u32(b.gen, g + 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_u32(b.gen) == g) {
+                if ((++spins & 255u) == 0) {
+                    if (globaltimer_ns() - t0 > limit_ns) {
+                        dev_fail(b.err, DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (*(volatile int32_t *)b.err != 0) {
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int32_t *)b.err != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+
+struct Ctx;  // per-handle allocation context
+
+// Device memory through the handle's allocator (stream ordered).
+struct Alloc {
+    homln_allocator a;
+    cudaStream_t stream;
+    void *get(size_t bytes);
+    void put(void *p, size_t bytes);
+};
+
+// A device buffer that frees itself through the allocator.
+template <typename T>
+struct DBuf {
+    Alloc *al = nullptr;
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept { *this = std::move(o); }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            al = o.al; p = o.p; n = o.n;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    bool alloc(Alloc *a, size_t count) {
+        release();
+        al = a;
+        n = count;
+        if (count == 0) return true;
+        p = static_cast<T *>(a->get(count * sizeof(T)));
+        if (!p) n = 0;
+        return p != nullptr;
+    }
+    void release() {
+        if (p && al) al->put(p, n * sizeof(T));
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// Thrown inside the library, caught at the C-ABI boundary.
+struct Error {
+    homln_status code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(homln_status code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define HCUDA(x) ::homln::check_cuda((x), #x)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Every kernel launch of the library goes through launch() so it can be counted.
+extern std::atomic<long long> g_kernel_launches;
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    kern<<<grid, block, smem, s>>>(args...);
+}
+
+// ---------------------------------------------------------------------------
+// Primitives (prims.cu)
+// ---------------------------------------------------------------------------
+// out[i] = sum_{j<i} in[j] (int64), total written to out[n]. `out` has n+1 entries.
+void scan_exclusive_i32(const int32_t *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s);
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s);
+// Stable LSD radix sort of 64-bit keys on bits [bit0, bit1), optional uint32 payload.
+// Result in keys/vals (the alternate buffers are scratch).
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit1, Alloc *al, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Graph building (graph.cu)
+// ---------------------------------------------------------------------------
+struct Csr {
+    int32_t n = 0;
+    int64_t nnz = 0;  // directed entries (2 x undirected edges)
+    DBuf<int64_t> rowptr;
+    DBuf<int32_t> col;
+};
+
+// Normalise an edge list (device int32 arrays) into a symmetric CSR with sorted rows.
+void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m, Csr &out, int32_t *d_err,
+               Alloc *al, cudaStream_t s);
+// Edges present in every CSR of `layers` (sorted-row intersection).
+void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s);
+// Undirected edge list u < v, ascending (u, v), of a CSR. Writes nnz/2 pairs.
+void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s);
+// Degree-descending relabelling: perm[new] = old; builds the relabelled CSR.
+void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Multi-source BFS (msbfs.cu)
+// ---------------------------------------------------------------------------
+struct BfsTuning {
+    int W = 0;           // words per node (0 = auto)
+    int push_alpha = 8;
+    int threads = 512;
+    int blocks_per_sm = 0;
+    int relabel = 1;
+};
+
+struct BfsStats {  // filled by an instrumented run
+    uint64_t levels = 0, pull_levels = 0, push_levels = 0;
+    uint64_t group_edges = 0;  // edges scanned by pull (per vertex, max over its lanes)
+    uint64_t lane_words = 0;   // 8-byte frontier words gathered by pull
+    uint64_t push_edges = 0;   // edges pushed
+    uint64_t batches = 0;
+    uint64_t push_words = 0;   // 8-byte atomic ORs issued by top-down levels
+    uint64_t sweep_bytes = 0;  // bytes of the per-level vertex sweeps (see msbfs.cu)
+    int words_per_node = 0;    // W of the last launch
+};
+
+// All-sources BFS: F[v] = sum of distances, R[v] = reachable count (v excluded).
+// ev_start/ev_stop (optional) are recorded on `s` right around the BFS kernel launch.
+void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuning &t, int32_t *d_err,
+                       Alloc *al, cudaStream_t s, BfsStats *stats, float *kernel_ms, cudaEvent_t ev_start = nullptr,
+                       cudaEvent_t ev_stop = nullptr);
+int msbfs_pick_words(int32_t n, int64_t nnz);
+
+// ---------------------------------------------------------------------------
+// Finalize / selection / composition / accuracy (select.cu)
+// ---------------------------------------------------------------------------
+void closeness_finalize(int32_t n, const int64_t *rowptr, const uint64_t *F, const uint32_t *R, double *cc,
+                        uint64_t *sumdist, int32_t *deg, cudaStream_t s);
+// Selected ids in rank order into d_out (capacity n); count to host.
+int32_t select_nodes(int32_t n, const double *d_scores, const homln_select &sel, int32_t *d_out,
+                     uint32_t *d_member_bits, int32_t *d_err, Alloc *al, cudaStream_t s);
+void cc2_scores(int32_t n, const std::vector<const uint64_t *> &sumdists, double *d_scores, Alloc *al,
+                cudaStream_t s);
+int32_t cc1_compose(int32_t n, const std::vector<const Csr *> &csrs, const std::vector<const uint64_t *> &sumdist,
+                    const std::vector<const int32_t *> &deg, const uint32_t *d_common_bits, double theta,
+                    int32_t *d_out, int32_t *d_err, Alloc *al, cudaStream_t s);
+int32_t bits_to_sorted_ids(int32_t n, const uint32_t *d_bits, int32_t *d_out, Alloc *al, cudaStream_t s);
+void bits_and(int32_t nwords, uint32_t *d_acc, const uint32_t *d_other, cudaStream_t s);
+void accuracy_counts(int32_t n, const int32_t *d_pred, int32_t n_pred, const int32_t *d_truth, int32_t n_truth,
+                     homln_accuracy_t *h_out, int32_t *d_err, Alloc *al, cudaStream_t s);
+
+}  // namespace homln

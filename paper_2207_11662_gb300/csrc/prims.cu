@@ -1,0 +1,223 @@
+// Device primitives: exclusive prefix sum and a stable LSD radix sort.
+// Used by CSR construction (sorting packed edge keys), relabelling and top-k
+// selection. Hand-written; no library kernels.
+#include "common.cuh"
+
+namespace homln {
+
+namespace {
+
+constexpr int SCAN_T = 512;
+constexpr int SCAN_I = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_I;
+
+template <typename T>
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+    __shared__ int64_t warp_tot[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < SCAN_T / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SCAN_T / 32) warp_tot[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    int64_t warp_base = warp > 0 ? warp_tot[warp - 1] : 0;
+    if (total) *total = warp_tot[SCAN_T / 32 - 1];
+    int64_t excl = warp_base + x - v;
+    __syncthreads();
+    return excl;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *__restrict__ in, int64_t n, int64_t *partials) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i)
+        if (base + i < n) s += (int64_t)in[base + i];
+    int64_t tot;
+    block_exclusive_scan<T>(s, &tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block totals in place; writes the grand total to *total.
+__global__ void __launch_bounds__(SCAN_T) k_scan_partials(int64_t *partials, int64_t nb, int64_t *total) {
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nb; base += SCAN_T) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < nb ? partials[i] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan<int64_t>(v, &tot);
+        if (i < nb) partials[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const T *__restrict__ in, int64_t *out, int64_t n,
+                                                     const int64_t *partials) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+    int64_t vals[SCAN_I];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        vals[i] = (base + i < n) ? (int64_t)in[base + i] : 0;
+        s += vals[i];
+    }
+    int64_t ex = block_exclusive_scan<T>(s, nullptr) + partials[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += vals[i];
+    }
+}
+
+template <typename T>
+void scan_impl(const T *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) {
+    if (n <= 0) {
+        HCUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return;
+    }
+    int64_t nb = ceil_div(n, SCAN_TILE);
+    DBuf<int64_t> part;
+    if (!part.alloc(al, nb)) fail(HOMLN_ENOMEM, "scan: partials");
+    launch(k_scan_reduce<T>, (unsigned)nb, SCAN_T, 0, s, in, n, part.p);
+    launch(k_scan_partials, 1, SCAN_T, 0, s, part.p, nb, out + n);
+    launch(k_scan_down<T>, (unsigned)nb, SCAN_T, 0, s, in, out, n, part.p);
+    HCUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort: 8-bit digits, one histogram / scan / scatter round per digit.
+// The scatter ranks each tile's items stably: every warp walks its 512 items
+// in index order, 32 at a time, grouping equal digits with match.any.
+// ---------------------------------------------------------------------------
+constexpr int RS_T = 256;
+constexpr int RS_WARPS = RS_T / 32;
+constexpr int RS_R = 16;  // rounds per warp
+constexpr int RS_TILE = RS_T * RS_R;
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                                                 uint32_t dmask, int32_t *counts, int64_t nb) {
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += RS_T) {
+        int64_t idx = base + i;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & dmask], 1);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                    uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                                                    int shift, uint32_t dmask, const int64_t *__restrict__ offsets,
+                                                    int64_t nb) {
+    __shared__ int32_t wcnt[RS_WARPS][256];
+    __shared__ int64_t boff[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_T) (&wcnt[0][0])[i] = 0;
+    boff[threadIdx.x] = offsets[(int64_t)threadIdx.x * nb + blockIdx.x];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_R * 32);
+    uint64_t k[RS_R];
+    uint32_t v[RS_R];
+    int32_t rank[RS_R];
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        int64_t idx = base + r * 32 + lane;
+        bool valid = idx < n;
+        k[r] = valid ? kin[idx] : 0ull;
+        if (VALS) v[r] = valid ? vin[idx] : 0u;
+        uint32_t d = valid ? (uint32_t)((k[r] >> shift) & dmask) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        int before = __popc(peers & ((1u << lane) - 1u));
+        int leader = __ffs(peers) - 1;
+        int cur = valid ? wcnt[warp][d] : 0;
+        __syncwarp();
+        if (valid && lane == leader) wcnt[warp][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[r] = cur + before;
+    }
+    __syncthreads();
+    {
+        int d = threadIdx.x;
+        int32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            int32_t t = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        int64_t idx = base + r * 32 + lane;
+        if (idx < n) {
+            uint32_t d = (uint32_t)((k[r] >> shift) & dmask);
+            int64_t dest = boff[d] + wcnt[warp][d] + rank[r];
+            kout[dest] = k[r];
+            if (VALS) vout[dest] = v[r];
+        }
+    }
+}
+
+}  // namespace
+
+void scan_exclusive_i32(const int32_t *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) {
+    scan_impl<int32_t>(in, out, n, al, s);
+}
+
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) {
+    scan_impl<int64_t>(in, out, n, al, s);
+}
+
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit1, Alloc *al, cudaStream_t s) {
+    if (n <= 1 || bit1 <= bit0) return;
+    int64_t nb = ceil_div(n, RS_TILE);
+    DBuf<uint64_t> kalt;
+    DBuf<uint32_t> valt;
+    DBuf<int32_t> counts;
+    DBuf<int64_t> offs;
+    if (!kalt.alloc(al, n) || (vals && !valt.alloc(al, n)) || !counts.alloc(al, 256 * nb) ||
+        !offs.alloc(al, 256 * nb + 1))
+        fail(HOMLN_ENOMEM, "radix sort scratch");
+    uint64_t *ka = keys, *kb = kalt.p;
+    uint32_t *va = vals, *vb = valt.p;
+    for (int shift = bit0; shift < bit1; shift += 8) {
+        int bits = bit1 - shift < 8 ? bit1 - shift : 8;
+        uint32_t dmask = (1u << bits) - 1u;
+        launch(k_rs_hist, (unsigned)nb, RS_T, 0, s, ka, n, shift, dmask, counts.p, nb);
+        scan_exclusive_i32(counts.p, offs.p, 256 * nb, al, s);
+        if (vals)
+            launch(k_rs_scatter<true>, (unsigned)nb, RS_T, 0, s, ka, va, kb, vb, n, shift, dmask, offs.p, nb);
+        else
+            launch(k_rs_scatter<false>, (unsigned)nb, RS_T, 0, s, ka, nullptr, kb, nullptr, n, shift, dmask, offs.p, nb);
+        HCUDA(cudaGetLastError());
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    if (ka != keys) {
+        HCUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        if (vals) HCUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+}  // namespace homln

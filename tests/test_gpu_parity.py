@@ -1,0 +1,329 @@
+"""GPU-vs-oracle parity through the C-ABI.
+
+Integer outputs (farness, reach, AND edge sets, CC-node lists, accuracy counts)
+must match bit for bit. Closeness values are one correctly rounded division of
+the same exact integers on both sides, so they are compared bit for bit too
+(stricter than the 1e-12 relative tolerance the path allows; the tolerance is
+used only where stated).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2207_11662_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def H():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2207_11662_gb300 import homln
+    return homln
+
+
+def to_dev(layers):
+    import torch
+    return [(torch.from_numpy(np.ascontiguousarray(s)).cuda(), torch.from_numpy(np.ascontiguousarray(d)).cuda())
+            for s, d in layers]
+
+
+def u64(t):
+    return t.cpu().numpy().astype(np.uint64)
+
+
+def check_graph(gF, gR, gcc, ref):
+    assert np.array_equal(u64(gF), ref["F"])
+    assert np.array_equal(gR.cpu().numpy().astype(np.uint32), ref["R"])
+    cc = gcc.cpu().numpy()
+    assert np.array_equal(cc, ref["cc"]), np.max(np.abs(cc - ref["cc"]))
+
+
+def full_parity(H, net, sels, tuning=None, heuristics=(0, 1, 2)):
+    g = H.Network(net.n, to_dev(net.layers), tuning=tuning)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    L = net.n_layers
+    for i in range(L):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    masks = sorted({(1 << L) - 1, 1, 3 if L >= 2 else 1})
+    for mask in masks:
+        s, d = g.and_aggregate(mask)
+        rs, rd = ref.and_edges(mask)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(d.cpu().numpy(), rd)
+        check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+        for sel, osel in sels:
+            gt = g.topk(-1, mask, sel)
+            assert gt.cpu().numpy().tolist() == ref.topk(-1, mask, osel).tolist()
+            for i in range(L):
+                assert g.topk(i, mask, sel).cpu().numpy().tolist() == ref.topk(i, mask, osel).tolist()
+            for heur in heuristics:
+                est = g.compose(mask, heur, sel)
+                want = ref.compose(mask, heur, osel)
+                assert est.cpu().numpy().tolist() == want.tolist(), (mask, heur)
+                acc = g.accuracy(est, gt)
+                wa = O.accuracy(want, ref.topk(-1, mask, osel))
+                for k in ("tp", "fp", "fn"):
+                    assert acc[k] == wa[k]
+                for k in ("jaccard", "precision", "recall", "f1"):
+                    assert acc[k] == pytest.approx(wa[k], rel=REL_TOL, abs=0)
+    g.close()
+
+
+def sels_all(H):
+    return [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5), O.Select(O.TOPK_PERCENT, 10.0, cc1_overlap=0.5)),
+            (H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=0.3), O.Select(O.GE_MEAN, cc1_overlap=0.3)),
+            (H.make_select(H.HOMLN_GT_MEAN), O.Select(O.GT_MEAN)),
+            (H.make_select(H.HOMLN_TOPK_COUNT, k=37, cc1_overlap=0.75), O.Select(O.TOPK_COUNT, k=37, cc1_overlap=0.75))]
+
+
+def test_small_er_config(H):
+    """3 independent ER layers, n = 1000, average degree 8 (the AND graph is almost empty)."""
+    full_parity(H, synth.homln_small_er(), sels_all(H))
+
+
+def test_small_overlap_config(H):
+    """The same shape with a shared edge pool, so the AND graph and the heuristics are non-trivial."""
+    full_parity(H, synth.homln_small_overlap(1000, 8.0, 3, 0.5, 111), sels_all(H))
+
+
+def test_hand_example(H):
+    import tests.test_oracle_pins as P
+    g = P.read_golden("hand_two_layer_example.txt")
+    n = int(g["n"][0])
+    net = synth.HoMLN(n, [P.edges_of(P.pairs_of(g["layer_x"])), P.edges_of(P.pairs_of(g["layer_y"]))])
+    full_parity(H, net, sels_all(H) + [(H.make_select(H.HOMLN_TOPK_COUNT, k=3), O.Select(O.TOPK_COUNT, k=3))])
+
+
+@pytest.mark.parametrize("W", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("relabel", [0, 1])
+def test_words_per_node_and_relabel(H, W, relabel):
+    """Every batch width and both vertex orders give identical results (ragged last batch included)."""
+    net = synth.homln_small_overlap(1537, 6.0, 2, 0.4, 5)
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    full_parity(H, net, sel, tuning=dict(words_per_node=W, relabel=relabel), heuristics=(2,))
+
+
+@pytest.mark.parametrize("alpha", [1, 1000000])
+def test_push_pull_extremes(H, alpha):
+    """alpha = 1: almost always bottom-up; alpha = 1e6: almost always top-down. Same answers."""
+    net = synth.HoMLN(3000, [synth.chung_lu_edges(3000, 12000, 9), synth.ba_edges(3000, 3, 10)])
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    full_parity(H, net, sel, tuning=dict(push_alpha=alpha, words_per_node=4), heuristics=(2,))
+
+
+def test_hubs_use_block_and_warp_tiers(H):
+    """A star plus a power-law layer: the centre's row exceeds the block threshold."""
+    n = 5000
+    star = (np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32))
+    cl = synth.chung_lu_edges(n, 25000, 77)
+    net = synth.HoMLN(n, [star, cl, synth.overlay(n, star, cl)])
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)),
+           (H.make_select(H.HOMLN_GE_MEAN), O.Select(O.GE_MEAN))]
+    for W in (2, 16):
+        full_parity(H, net, sel, tuning=dict(words_per_node=W, threads=256))
+
+
+def test_degenerate_graphs(H):
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)),
+           (H.make_select(H.HOMLN_GE_MEAN), O.Select(O.GE_MEAN))]
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32))
+    # a single node, no edges
+    full_parity(H, synth.HoMLN(1, [empty, empty]), sel)
+    # two nodes joined in one layer only
+    full_parity(H, synth.HoMLN(2, [(np.array([0], np.int32), np.array([1], np.int32)), empty]), sel)
+    # self loops and duplicates only
+    loops = (np.array([3, 3, 5, 5], np.int32), np.array([3, 3, 5, 5], np.int32))
+    full_parity(H, synth.HoMLN(7, [loops, loops]), sel)
+    # many small components with a ragged batch
+    n = 4099
+    e = synth.er_edges(n, 1500, 3)
+    full_parity(H, synth.HoMLN(n, [e, synth.noisy_copy(n, e, 4)]), sel)
+
+
+def test_path_and_cycle_closed_forms(H):
+    """Long diameters (thousands of levels) against the closed forms directly."""
+    n = 3000
+    path = (np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32))
+    cyc = (np.arange(n, dtype=np.int32), ((np.arange(n) + 1) % n).astype(np.int32))
+    g = H.Network(n, to_dev([path, cyc]))
+    F, R, _ = g.layer_closeness(0)
+    i = np.arange(n, dtype=np.uint64)
+    want = i * (i + 1) // 2 + (n - 1 - i) * (n - i) // 2
+    assert np.array_equal(u64(F), want)
+    F, R, _ = g.layer_closeness(1)
+    assert np.all(u64(F) == n * n // 4)
+    g.close()
+
+
+def test_host_buffers_match_device_buffers(H):
+    net = synth.homln_small_overlap(800, 8.0, 2, 0.5, 21)
+    ref = O.OracleHoMLN(net.n, net.layers)
+    h = H.homln_create(net.n, net.layers)  # host edge lists
+    F = np.zeros(net.n, np.uint64)
+    R = np.zeros(net.n, np.uint32)
+    cc = np.zeros(net.n, np.float64)
+    H.homln_layer_closeness(h, 1, F, R, cc)
+    assert np.array_equal(F, ref.layer(1)["F"]) and np.array_equal(R, ref.layer(1)["R"])
+    assert np.array_equal(cc, ref.layer(1)["cc"])
+    m = H.homln_and_aggregate(h, 3)
+    s = np.zeros(m, np.int32)
+    d = np.zeros(m, np.int32)
+    assert H.homln_and_aggregate(h, 3, m, s, d) == m
+    rs, rd = ref.and_edges(3)
+    assert np.array_equal(s, rs) and np.array_equal(d, rd)
+    out = np.zeros(net.n, np.int32)
+    sel = H.make_select()
+    c = H.homln_compose(h, 3, H.HOMLN_CC2, sel, out)
+    assert out[:c].tolist() == ref.compose(3, O.CC2, O.Select()).tolist()
+    gt = np.zeros(net.n, np.int32)
+    cg = H.homln_topk(h, -1, 3, sel, gt)
+    acc = H.homln_accuracy(h, out, c, gt, cg)
+    want = O.accuracy(out[:c], gt[:cg])
+    assert (acc["tp"], acc["fp"], acc["fn"]) == (want["tp"], want["fp"], want["fn"])
+    H.homln_destroy(h)
+
+
+def test_error_statuses(H):
+    n = 50
+    bad = (np.array([0, 50], np.int32), np.array([1, 2], np.int32))
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_create(n, [bad])
+    assert e.value.code == H.HOMLN_EINVAL
+    neg = (np.array([-1], np.int32), np.array([1], np.int32))
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_create(n, [neg])
+    assert e.value.code == H.HOMLN_EINVAL
+    good = synth.er_edges(n, 100, 1)
+    h = H.homln_create(n, [good, good])
+    for mask in (0, 4, 1 << 63):
+        with pytest.raises(H.HomlnError) as e:
+            H.homln_and_aggregate(h, mask)
+        assert e.value.code == H.HOMLN_EINVAL
+    m = H.homln_and_aggregate(h, 3)
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_and_aggregate(h, 3, m - 1, np.zeros(m, np.int32), np.zeros(m, np.int32))
+    assert e.value.code == H.HOMLN_ERANGE
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_layer_closeness(h, 2, None, None, None)
+    assert e.value.code == H.HOMLN_EINVAL
+    out = np.zeros(n, np.int32)
+    for sel in (H.make_select(7), H.make_select(H.HOMLN_TOPK_PERCENT, 101.0), H.make_select(H.HOMLN_TOPK_COUNT, k=-1),
+                H.make_select(cc1_overlap=1.5)):
+        with pytest.raises(H.HomlnError) as e:
+            H.homln_compose(h, 3, H.HOMLN_CC1, sel, out)
+        assert e.value.code == H.HOMLN_EINVAL
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_compose(h, 3, 9, H.make_select(), out)
+    assert e.value.code == H.HOMLN_EINVAL
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_accuracy(h, np.array([0, 60], np.int32), 2, np.array([1], np.int32), 1)
+    assert e.value.code == H.HOMLN_EINVAL
+    # the handle still works after every rejected call
+    F = np.zeros(n, np.uint64)
+    H.homln_layer_closeness(h, 0, F, None, None)
+    assert np.array_equal(F, O.OracleHoMLN(n, [good]).layer(0)["F"])
+    H.homln_destroy(h)
+
+
+def test_allocator_failure_and_torch_allocator(H):
+    """A caller allocator that fails on its k-th call gives ENOMEM and leaks nothing it handed out."""
+    import ctypes
+    import torch
+    net = synth.homln_small_overlap(700, 6.0, 2, 0.5, 3)
+    live = {}
+    calls = [0]
+    fail_at = [10 ** 9]
+
+    @H.ALLOC_FN
+    def alloc(ctx, nbytes, stream):
+        calls[0] += 1
+        if calls[0] == fail_at[0]:
+            return None
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @H.FREE_FN
+    def free(ctx, p, nbytes, stream):
+        live.pop(int(p))
+
+    a = H.homln_allocator(None, alloc, free)
+    h = H.homln_create(net.n, to_dev(net.layers), allocator=a)
+    F = torch.empty(net.n, dtype=torch.int64, device="cuda")
+    H.homln_layer_closeness(h, 0, F, None, None)
+    H.homln_destroy(h)
+    torch.cuda.synchronize()
+    assert not live
+    total = calls[0]
+    assert total > 5
+    for k in (1, 2, total // 2, total - 1):
+        calls[0] = 0
+        fail_at[0] = k
+        try:
+            h = H.homln_create(net.n, to_dev(net.layers), allocator=a)
+            try:
+                H.homln_layer_closeness(h, 0, F, None, None)
+            except H.HomlnError as e:
+                assert e.value.code == H.HOMLN_ENOMEM if hasattr(e, "value") else e.code == H.HOMLN_ENOMEM
+            H.homln_destroy(h)
+        except H.HomlnError as e:
+            assert e.code == H.HOMLN_ENOMEM
+        torch.cuda.synchronize()
+        assert not live, f"leak after failing allocation {k}"
+    # torch's caching allocator as the backend
+    ta = H.torch_allocator()
+    g = H.Network(net.n, to_dev(net.layers), allocator=ta)
+    Fg, _, _ = g.layer_closeness(1)
+    assert np.array_equal(u64(Fg), O.OracleHoMLN(net.n, net.layers).layer(1)["F"])
+    g.close()
+
+
+def test_powerlaw_full_size_sampled(H):
+    """4 Chung-Lu layers on 50,000 nodes (the benchmark workload), in the benchmark's launch configuration;
+    F and R checked at a seeded 2,000-vertex sample by oracle BFS from those vertices, the rest by properties."""
+    import torch
+    net = synth.homln_powerlaw()
+    n, L = net.n, net.n_layers
+    g = H.Network(n, to_dev(net.layers))
+    rng = np.random.default_rng(2001)
+    sample = np.sort(rng.choice(n, 2000, replace=False)).astype(np.int32)
+    keys = [O.edge_keys(n, s, d) for s, d in net.layers]
+    graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
+    outs = [g.layer_closeness(i) for i in range(L)] + [g.and_closeness((1 << L) - 1)]
+    for (rp, col), (F, R, cc) in zip(graphs, outs):
+        Fs, Rs = O.farness_reach(n, rp, col, sources=sample, threads=8)
+        assert np.array_equal(u64(F)[sample], Fs)
+        assert np.array_equal(R.cpu().numpy().astype(np.uint32)[sample], Rs)
+        assert np.array_equal(cc.cpu().numpy()[sample], O.wf_closeness(n, Fs, Rs))
+        # properties at every vertex: sum over v of F equals sum over v of R-weighted distances is symmetric;
+        # R is |component| - 1, so vertices of one component share R; F >= R
+        Fa, Ra = u64(F), R.cpu().numpy().astype(np.uint64)
+        assert np.all(Fa >= Ra)
+        assert np.all((Ra == 0) == (Fa == 0))
+    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0)
+    k = O.topk_count(O.Select(), n)
+    for which in list(range(L)) + [-1]:
+        top = g.topk(which, (1 << L) - 1, sel).cpu().numpy()
+        cc = (outs[which][2] if which >= 0 else outs[-1][2]).cpu().numpy()
+        assert top.shape[0] == k and len(set(top.tolist())) == k
+        # ranking property: scores non-increasing, ties by ascending id, nothing outside beats the last one
+        s = cc[top]
+        assert np.all(s[:-1] >= s[1:])
+        tie = s[:-1] == s[1:]
+        assert np.all(top[:-1][tie] < top[1:][tie])
+        rest = np.setdiff1d(np.arange(n), top)
+        assert np.all((cc[rest] < s[-1]) | ((cc[rest] == s[-1]) & (rest > top[-1])))
+    naive = g.compose((1 << L) - 1, H.HOMLN_NAIVE, sel).cpu().numpy()
+    cc1 = g.compose((1 << L) - 1, H.HOMLN_CC1, sel).cpu().numpy()
+    cc2 = g.compose((1 << L) - 1, H.HOMLN_CC2, sel).cpu().numpy()
+    assert set(cc1.tolist()) <= set(naive.tolist())
+    for i in range(L):
+        assert set(naive.tolist()) <= set(g.topk(i, 1, sel).cpu().numpy().tolist())
+    assert cc2.shape[0] == k and np.all(np.diff(cc2) > 0)
+    g.close()
+    torch.cuda.synchronize()
