@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--cpu-sample-sources", type=int, default=1500)
     p.add_argument("--words", type=int, default=0, help="BFS words per node (0 = auto)")
     p.add_argument("--alpha", type=int, default=0)
+    p.add_argument("--single-bfs", action="store_true",
+                   help="profiling aid: build the workload, run one layer's all-sources BFS once, exit")
+    p.add_argument("--launch-list", action="store_true",
+                   help="profiling aid: run exactly one plain step (no warm-up, no instrumented pass), exit")
     return p.parse_args()
 
 
@@ -156,11 +160,9 @@ def peaks():
 
 
 def bfs_bytes(prof: dict) -> float:
-    """Algorithmic bytes of the BFS launches (the byte model is stated in the design doc):
-    gathered frontier words (8 B) + column indices of scanned and pushed edges (4 B) +
-    pushed words (8 B atomic OR) + the per-level vertex sweeps counted by the library."""
-    return (8.0 * prof["words_gathered"] + 4.0 * (prof["edges_scanned"] + prof["edges_pushed"]) +
-            8.0 * prof["words_pushed"] + float(prof["sweep_bytes"]))
+    """Algorithmic bytes of the BFS launches (the byte model is stated in the design doc): the bytes
+    the kernel's loads and stores request, counted by its instrumented variant."""
+    return float(prof["bytes"])
 
 
 def run_ours(args, rank, world, dist):
@@ -218,6 +220,19 @@ def run_ours(args, rank, world, dist):
         finally:
             H.homln_destroy(h)
 
+    if args.single_bfs:
+        h = H.homln_create(n, dlayers, stream=stream.cuda_stream)
+        if tuning:
+            H.homln_set_tuning(h, **tuning)
+        F = torch.empty(n, dtype=torch.int64, device=dev)
+        H.homln_layer_closeness(h, 0, F, None, None)
+        H.homln_destroy(h)
+        torch.cuda.synchronize()
+        return None, net
+    if args.launch_list:
+        step(dlayers)
+        torch.cuda.synchronize()
+        return None, net
     # warm-up
     for _ in range(args.warmup):
         step(dlayers)
@@ -303,7 +318,7 @@ def run_ours(args, rank, world, dist):
                                      for nm, a in zip(("naive", "cc1", "cc2"), accs)},
         "bfs_profile": {k: prof_count[k] for k in ("levels", "pull_levels", "push_levels", "batches",
                                                    "edges_scanned", "words_gathered", "edges_pushed",
-                                                   "words_pushed", "sweep_bytes", "words_per_node")},
+                                                   "words_pushed", "bytes", "visits", "words_per_node")},
     }
     result["value"] = round(work * world * args.steps / t_max / 1e9, 3)
     return result, net
@@ -362,6 +377,8 @@ def main():
         tdist.init_process_group("nccl", init_method="env://")
         dist = tdist
     result, net = run_ours(args, rank, world, dist)
+    if result is None:
+        return
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)

@@ -210,7 +210,9 @@ typedef struct homln_profile_t {
     int64_t words_gathered;     /* 8-byte frontier words read by bottom-up levels */
     int64_t edges_pushed;       /* top-down neighbour visits */
     int64_t words_pushed;       /* 8-byte atomic ORs of top-down levels */
-    int64_t sweep_bytes;        /* bytes of the per-level vertex sweeps (seen, next, rowptr, accumulator) */
+    int64_t bytes;              /* bytes the BFS kernels' loads and stores request (a load shared by the
+                                   lanes of one vertex counted once): the algorithmic bytes */
+    int64_t visits;             /* vertex visits: non-skipped vertices processed, summed over levels */
     int32_t words_per_node;     /* W of the last instrumented launch */
     int32_t reserved;
 } homln_profile_t;

@@ -203,7 +203,8 @@ void analyse(homln_t h, GraphState &g) {
         h->stats.push_edges += st.push_edges;
         h->stats.batches += st.batches;
         h->stats.push_words += st.push_words;
-        h->stats.sweep_bytes += st.sweep_bytes;
+        h->stats.bytes += st.bytes;
+        h->stats.visits += st.visits;
         h->stats.words_per_node = st.words_per_node;
     }
     h->bfs_launches += 1;
@@ -531,7 +532,8 @@ homln_status homln_get_profile(homln_t h, homln_profile_t *out) {
     out->words_gathered = (int64_t)h->stats.lane_words;
     out->edges_pushed = (int64_t)h->stats.push_edges;
     out->words_pushed = (int64_t)h->stats.push_words;
-    out->sweep_bytes = (int64_t)h->stats.sweep_bytes;
+    out->bytes = (int64_t)h->stats.bytes;
+    out->visits = (int64_t)h->stats.visits;
     out->words_per_node = h->stats.words_per_node;
     out->reserved = 0;
     API_END

@@ -215,7 +215,8 @@ struct BfsStats {  // filled by an instrumented run
     uint64_t push_edges = 0;   // edges pushed
     uint64_t batches = 0;
     uint64_t push_words = 0;   // 8-byte atomic ORs issued by top-down levels
-    uint64_t sweep_bytes = 0;  // bytes of the per-level vertex sweeps (see msbfs.cu)
+    uint64_t bytes = 0;        // bytes requested by the kernel's loads/stores (broadcast loads once)
+    uint64_t visits = 0;       // vertex visits (non-quiet vertices processed per level)
     int words_per_node = 0;    // W of the last launch
 };
 

@@ -32,7 +32,8 @@ struct BfsArgs {
     uint64_t *seen;
     uint64_t *fa;
     uint64_t *fb;
-    uint64_t *acc;  // push accumulator; all zero between phases
+    uint64_t *acc;     // top-down accumulator; all zero between phases
+    uint8_t *quiet;    // per vertex: levels since its seen word became full (saturates at 2)
     uint64_t *F;
     uint32_t *R;
     unsigned long long *ctr;  // 3 slots x {new bits, frontier edges, unfinished edges, spare}
@@ -44,7 +45,14 @@ struct BfsArgs {
     unsigned long long *stats;
 };
 
-enum { ST_LEVELS, ST_PULL, ST_PUSH, ST_EDGES, ST_WORDS, ST_PUSHED, ST_BATCHES, ST_PUSHWORDS, ST_N };
+// A vertex is "quiet" once its seen word has been full at the start of two levels: both
+// frontier buffers then hold zero for it and nothing can change it, so every later level
+// of the batch skips it after reading one byte.
+constexpr uint8_t QUIET = 2;
+
+enum {
+    ST_LEVELS, ST_PULL, ST_PUSH, ST_EDGES, ST_WORDS, ST_PUSHED, ST_BATCHES, ST_PUSHWORDS, ST_BYTES, ST_VISITS, ST_N
+};
 
 template <int W>
 struct Geo {
@@ -85,6 +93,13 @@ __device__ __forceinline__ bool group_any(bool b) {
 #pragma unroll
     for (int o = T / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
     return v != 0;
+}
+
+template <int T>
+__device__ __forceinline__ int64_t group_max(int64_t v) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, o));
+    return v;
 }
 
 template <int K>
@@ -169,10 +184,12 @@ __device__ __forceinline__ void reset_next_slot(const BfsArgs &a, uint32_t ps) {
 }
 
 // Record the new bits of v (already reduced to this lane's K words) and its counters.
+// full0: the vertex's seen word was already full when the level started (its new bits are 0).
 template <int W, bool STATS>
 __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool writer, int64_t v, int q,
                                               const uint64_t (&s)[Geo<W>::K], const uint64_t (&nw)[Geo<W>::K],
-                                              uint64_t *nxt, int level, int64_t deg, PhaseCounters &c) {
+                                              uint64_t *nxt, int level, int64_t deg, bool full0, uint8_t qv,
+                                              PhaseCounters &c, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     bool any = false, full = true;
     uint32_t cnt = 0;
@@ -187,6 +204,7 @@ __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool w
     if (act && writer) {
         if (any) stw<K>(a.seen + v * W + q * K, ns);
         stw<K>(nxt + v * W + q * K, nw);
+        if (STATS) st[ST_BYTES] += (any ? 16 : 8) * K;
     }
     cnt = group_sum<T>(cnt);
     bool gfull = !group_any<T>(!full);
@@ -196,8 +214,11 @@ __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool w
             a.R[v] += cnt;
             c.newbits += cnt;
             c.mf += (unsigned long long)deg;
+            if (STATS) st[ST_BYTES] += 24;
         }
         if (!gfull) c.mu += (unsigned long long)deg;
+        if (full0) a.quiet[v] = qv + 1;
+        if (STATS) st[ST_VISITS] += 1;
     }
 }
 
@@ -205,8 +226,8 @@ __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool w
 
 // Level 0 and 1 of a batch: seen = own source bit (plus padding bits for a short
 // last batch); every source ORs its bit into its neighbours' accumulators.
-template <int W>
-__device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns) {
+template <int W, bool STATS>
+__device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns, unsigned long long *st) {
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
@@ -221,6 +242,8 @@ __device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns) {
             if ((b >> 6) == wi) x |= 1ull << (b & 63);
         }
         a.seen[i] = x;
+        if (wi == 0) a.quiet[v] = 0;
+        if (STATS) st[ST_BYTES] += 8 + (wi == 0);
     }
     const int64_t e0 = a.rowptr[s0], e1 = a.rowptr[s0 + ns];
     for (int64_t e = e0 + gtid; e < e1; e += nthreads) {
@@ -231,21 +254,29 @@ __device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns) {
         }
         const int32_t u = __ldg(a.col + e);
         atomicOr(reinterpret_cast<unsigned long long *>(a.acc + (int64_t)u * W + (lo >> 6)), 1ull << (lo & 63));
+        if (STATS) { st[ST_BYTES] += 4 + 8; st[ST_PUSHED] += 1; st[ST_PUSHWORDS] += 1; }
     }
 }
 
 // Keep the accumulated bits not yet seen: they become the next frontier.
 template <int W, bool STATS>
-__device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c) {
+__device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c,
+                               unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     reset_next_slot(a, ps);
     const int lane = threadIdx.x & 31, q = lane % T;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t G = ((int64_t)gridDim.x * blockDim.x) / T;
     for (int64_t v = gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-        const bool act = v < a.n;
+        uint8_t qv = 0;
+        if (v < a.n) {
+            qv = a.quiet[v];
+            if (STATS && q == 0) st[ST_BYTES] += 1;
+        }
+        const bool act = v < a.n && qv < QUIET;
         uint64_t s[K], z[K], nw[K];
         int64_t deg = 0;
+        bool lane_full = true;
 #pragma unroll
         for (int k = 0; k < K; ++k) s[k] = z[k] = nw[k] = 0;
         if (act) {
@@ -256,6 +287,7 @@ __device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint3
             for (int k = 0; k < K; ++k) {
                 nw[k] = z[k] & ~s[k];
                 nz |= z[k] != 0;
+                lane_full &= s[k] == ~0ull;
             }
             if (nz) {
                 uint64_t zero[K];
@@ -264,8 +296,10 @@ __device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint3
                 stw<K>(a.acc + v * W + q * K, zero);
             }
             deg = a.rowptr[v + 1] - a.rowptr[v];
+            if (STATS) st[ST_BYTES] += (nz ? 24 : 16) * K + (q == 0 ? 16 : 0);
         }
-        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, c);
+        const bool full0 = !group_any<T>(!lane_full);
+        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, full0, qv, c, st);
     }
     flush_counters(a, c, ps);
 }
@@ -284,6 +318,9 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
         __shared__ uint64_t red[32][16][2];
         const int S = blockDim.x / T, p = threadIdx.x / T;
         for (int64_t v = blockIdx.x; v < a.hub_block_end; v += gridDim.x) {
+            const uint8_t qv = a.quiet[v];
+            if (STATS && threadIdx.x == 0) st[ST_BYTES] += 1;
+            if (qv >= QUIET) continue;  // uniform over the block
             uint64_t s[K], need[K], acc[K];
             ldw<K>(a.seen + v * W + q * K, s);
             bool lane_need = false;
@@ -293,10 +330,16 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                 acc[k] = 0;
                 lane_need |= need[k] != 0;
             }
+            const bool full0 = __syncthreads_or(lane_need ? 1 : 0) == 0;
             const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
-            if (lane_need) {
-                int64_t it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
-                if (STATS) { st[ST_WORDS] += it * K; st[ST_EDGES] += it; }
+            int64_t it = 0;
+            if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
+            if (STATS) {
+                st[ST_WORDS] += it * K;
+                st[ST_BYTES] += it * 8 * K;
+                int64_t gm = group_max<T>(it);
+                if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
+                if (p == 0) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
             }
 #pragma unroll
             for (int o = T; o < 32; o <<= 1)
@@ -316,7 +359,7 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                         for (int k = 0; k < K; ++k) t[k] |= red[w][lane][k];
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = t[k] & need[k];
-                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, c);
+                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
             }
             __syncthreads();
         }
@@ -327,6 +370,9 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
         const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const int64_t NW = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) {
+            const uint8_t qv = a.quiet[v];
+            if (STATS && lane == 0) st[ST_BYTES] += 1;
+            if (qv >= QUIET) continue;  // uniform over the warp
             uint64_t s[K], need[K], acc[K], nw[K];
             ldw<K>(a.seen + v * W + q * K, s);
             bool lane_need = false;
@@ -336,10 +382,16 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                 acc[k] = 0;
                 lane_need |= need[k] != 0;
             }
+            const bool full0 = !__any_sync(0xffffffffu, lane_need);
             const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
-            if (lane_need) {
-                int64_t it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
-                if (STATS) { st[ST_WORDS] += it * K; st[ST_EDGES] += it; }
+            int64_t it = 0;
+            if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
+            if (STATS) {
+                st[ST_WORDS] += it * K;
+                st[ST_BYTES] += it * 8 * K;
+                int64_t gm = group_max<T>(it);
+                if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
+                if (p == 0) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
             }
 #pragma unroll
             for (int o = T; o < 32; o <<= 1)
@@ -347,7 +399,7 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                 for (int k = 0; k < K; ++k) acc[k] |= __shfl_xor_sync(0xffffffffu, acc[k], o);
 #pragma unroll
             for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, c);
+            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
         }
     }
     // --- group tier: T lanes per vertex
@@ -355,7 +407,12 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
         const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const int64_t G = ((int64_t)gridDim.x * blockDim.x) / T;
         for (int64_t v = a.hub_warp_end + gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-            const bool act = v < a.n;
+            uint8_t qv = 0;
+            if (v < a.n) {
+                qv = a.quiet[v];
+                if (STATS && q == 0) st[ST_BYTES] += 1;
+            }
+            const bool act = v < a.n && qv < QUIET;
             uint64_t s[K], need[K], acc[K], nw[K];
             bool lane_need = false;
             int64_t rb = 0, re = 0;
@@ -371,27 +428,38 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                 rb = a.rowptr[v];
                 re = a.rowptr[v + 1];
             }
-            if (lane_need) {
-                int64_t it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
-                if (STATS) { st[ST_WORDS] += it * K; st[ST_EDGES] += it; }
+            // every lane must take part in the shuffle, so no short-circuit around it
+            const bool group_needs = group_any<T>(lane_need);
+            const bool full0 = act && !group_needs;
+            int64_t it = 0;
+            if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
+            if (STATS) {
+                st[ST_WORDS] += it * K;
+                st[ST_BYTES] += it * 8 * K;
+                int64_t gm = group_max<T>(it);
+                if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
+                if (act) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-            commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, c);
+            commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
         }
     }
     flush_counters(a, c, ps);
 }
 
-// Top-down level: frontier vertices OR their words into the neighbours' accumulators.
+// Top-down level: frontier vertices OR their words into the neighbours' accumulators
+// (quiet neighbours are full and are skipped).
 template <int W, bool STATS>
 __device__ void phase_push(const BfsArgs &a, const uint64_t *__restrict__ cur, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
     auto push_row = [&](int64_t v, int p, int S) {
+        if (a.quiet[v] >= QUIET) return;  // a quiet vertex has an all-zero frontier word
         uint64_t f[K];
         ldw<K>(cur + v * W + q * K, f);
+        if (STATS) st[ST_BYTES] += 8 * K + 1;
         bool any = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) any |= f[k] != 0;
@@ -399,13 +467,14 @@ __device__ void phase_push(const BfsArgs &a, const uint64_t *__restrict__ cur, u
         const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
         for (int64_t j = rb + p; j < re; j += S) {
             const int64_t u = __ldg(a.col + j);
+            if (STATS && q == 0) { st[ST_PUSHED] += 1; st[ST_BYTES] += 5; }
+            if (a.quiet[u] >= QUIET) continue;
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (f[k]) {
                     atomicOr(reinterpret_cast<unsigned long long *>(a.acc + u * W + q * K + k), f[k]);
-                    if (STATS) st[ST_PUSHWORDS] += 1;
+                    if (STATS) { st[ST_PUSHWORDS] += 1; st[ST_BYTES] += 8; }
                 }
-            if (STATS && q == 0) st[ST_PUSHED] += 1;
         }
     };
     for (int64_t v = blockIdx.x; v < a.hub_block_end; v += gridDim.x) push_row(v, threadIdx.x / T, blockDim.x / T);
@@ -418,7 +487,7 @@ __device__ void phase_push(const BfsArgs &a, const uint64_t *__restrict__ cur, u
 }
 
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512) k_msbfs(BfsArgs a) {
+__global__ void __launch_bounds__(512, 2) k_msbfs(BfsArgs a) {
     PhaseCounters c;
     unsigned long long st[ST_N];
 #pragma unroll
@@ -427,9 +496,9 @@ __global__ void __launch_bounds__(512) k_msbfs(BfsArgs a) {
     for (int32_t b = 0; b < a.nbatches; ++b) {
         const int32_t s0 = b * 64 * W;
         const int32_t ns = min(64 * W, a.n - s0);
-        phase_start_batch<W>(a, s0, ns);
+        phase_start_batch<W, STATS>(a, s0, ns, st);
         if (!grid_sync(a.bar)) return;
-        phase_finalize<W, STATS>(a, a.fa, 1, ps, c);
+        phase_finalize<W, STATS>(a, a.fa, 1, ps, c, st);
         ++ps;
         if (!grid_sync(a.bar)) return;
         uint64_t *cur = a.fa, *nxt = a.fb;
@@ -442,7 +511,7 @@ __global__ void __launch_bounds__(512) k_msbfs(BfsArgs a) {
             if (push) {
                 phase_push<W, STATS>(a, cur, st);
                 if (!grid_sync(a.bar)) return;
-                phase_finalize<W, STATS>(a, nxt, level, ps, c);
+                phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
             } else {
                 phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st);
             }
@@ -463,6 +532,8 @@ __global__ void __launch_bounds__(512) k_msbfs(BfsArgs a) {
         atomicAdd(a.stats + ST_WORDS, st[ST_WORDS]);
         atomicAdd(a.stats + ST_PUSHED, st[ST_PUSHED]);
         atomicAdd(a.stats + ST_PUSHWORDS, st[ST_PUSHWORDS]);
+        atomicAdd(a.stats + ST_BYTES, st[ST_BYTES]);
+        atomicAdd(a.stats + ST_VISITS, st[ST_VISITS]);
     }
 }
 
@@ -534,11 +605,13 @@ void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuni
     }
     const size_t words = (size_t)n * W;
     DBuf<uint64_t> seen, fa, fb, acc, Fi;
+    DBuf<uint8_t> quiet;
     DBuf<uint32_t> Ri;
     DBuf<unsigned long long> ctr, st;
     DBuf<uint32_t> barmem;
     DBuf<int32_t> tiers;
     if (!seen.alloc(al, words) || !fa.alloc(al, words) || !fb.alloc(al, words) || !acc.alloc(al, words) ||
+        !quiet.alloc(al, (size_t)n) ||
         !ctr.alloc(al, 12) || !barmem.alloc(al, 2) || !tiers.alloc(al, 2))
         fail(HOMLN_ENOMEM, "bfs state");
     uint64_t *F = d_F;
@@ -585,6 +658,7 @@ void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuni
     a.fa = fa.p;
     a.fb = fb.p;
     a.acc = acc.p;
+    a.quiet = quiet.p;
     a.F = F;
     a.R = R;
     a.ctr = ctr.p;
@@ -628,11 +702,8 @@ void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuni
         stats->push_edges += h[ST_PUSHED];
         stats->batches += h[ST_BATCHES];
         stats->push_words += h[ST_PUSHWORDS];
-        // per level: seen read + write, next write (8 W n bytes each) and rowptr (8 (n+1));
-        // per top-down level: accumulator read + clear; per batch: seen initialisation
-        const double nW = 8.0 * (double)n * W;
-        stats->sweep_bytes += (uint64_t)(h[ST_LEVELS] * (3.0 * nW + 8.0 * (n + 1)) + h[ST_PUSH] * 2.0 * nW +
-                                         h[ST_BATCHES] * nW);
+        stats->bytes += h[ST_BYTES];
+        stats->visits += h[ST_VISITS];
     }
     if (stats) stats->words_per_node = W;
 }

@@ -58,7 +58,7 @@ class homln_profile_t(ctypes.Structure):
     _fields_ = [("bfs_launches", c_int64), ("bfs_timed_launches", c_int64), ("bfs_ms", c_double),
                 ("levels", c_int64), ("pull_levels", c_int64), ("push_levels", c_int64), ("batches", c_int64),
                 ("edges_scanned", c_int64), ("words_gathered", c_int64), ("edges_pushed", c_int64),
-                ("words_pushed", c_int64), ("sweep_bytes", c_int64), ("words_per_node", c_int32),
+                ("words_pushed", c_int64), ("bytes", c_int64), ("visits", c_int64), ("words_per_node", c_int32),
                 ("reserved", c_int32)]
 
     def as_dict(self):
