@@ -194,6 +194,25 @@ HOMLN_API homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heu
 HOMLN_API homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, const int32_t *truth,
                             int32_t n_truth, homln_accuracy_t *out);
 
+/* Accuracy without device allocation (the paper has no counterpart: this is an interface
+ * for callers that cannot call cudaMalloc, e.g. because another allocator already owns the
+ * GPU's memory or because their loop must never enter an allocator; every handle-based call
+ * allocates, so this one takes no handle).
+ *   n_nodes      node universe, 1 <= n_nodes <= HOMLN_NOALLOC_MAX_NODES (larger: EINVAL).
+ *   pred, truth  int32 node-id lists in DEVICE memory (host pointers: EINVAL); duplicates ignored.
+ *   stream       cudaStream_t to run on (NULL = legacy default stream).
+ *   out          host output; the call synchronises `stream` before returning.
+ * Same results as homln_accuracy. Scratch is one static device array (two 2^20-bit bitmaps
+ * and a few counters, about 256 KB) that every GPU loading the library keeps until exit; it
+ * allocates nothing and calls no allocating routine. The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture. All calls share the array and each clears what it uses: calls
+ * that overlap on the GPU (other streams or threads) race -- serialise them. */
+#define HOMLN_NOALLOC_MAX_NODES 1048576
+HOMLN_API homln_status homln_accuracy_noalloc(int32_t n_nodes, const int32_t *pred, int32_t n_pred,
+                                              const int32_t *truth, int32_t n_truth, void *stream,
+                                              homln_accuracy_t *out);
+
 /* Measurement support (no counterpart in the paper; used by the benchmark).
  * homln_set_profiling: timing != 0 records CUDA events on the handle's stream right
  * around every BFS kernel launch; instrument != 0 runs the BFS kernels in a

@@ -244,5 +244,8 @@ int32_t bits_to_sorted_ids(int32_t n, const uint32_t *d_bits, int32_t *d_out, Al
 void bits_and(int32_t nwords, uint32_t *d_acc, const uint32_t *d_other, cudaStream_t s);
 void accuracy_counts(int32_t n, const int32_t *d_pred, int32_t n_pred, const int32_t *d_truth, int32_t n_truth,
                      homln_accuracy_t *h_out, int32_t *d_err, Alloc *al, cudaStream_t s);
+void accuracy_counts_prealloc(int32_t n, const int32_t *d_pred, int32_t n_pred, const int32_t *d_truth,
+                              int32_t n_truth, uint32_t *bits_p, uint32_t *bits_t, unsigned long long *c3, double *r4,
+                              int32_t *err, homln_accuracy_t *h_out, int32_t *h_err, cudaStream_t s);
 
 }  // namespace homln

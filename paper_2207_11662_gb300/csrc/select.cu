@@ -564,4 +564,34 @@ void accuracy_counts(int32_t n, const int32_t *d_pred, int32_t n_pred, const int
     h_out->f1 = r[3];
 }
 
+// The accuracy kernels run on scratch the caller provides (no allocation here).
+// bits_p/bits_t hold ceil(n/32) words each; c3 three counters; r4 four doubles; err one word.
+void accuracy_counts_prealloc(int32_t n, const int32_t *d_pred, int32_t n_pred, const int32_t *d_truth,
+                              int32_t n_truth, uint32_t *bits_p, uint32_t *bits_t, unsigned long long *c3, double *r4,
+                              int32_t *err, homln_accuracy_t *h_out, int32_t *h_err, cudaStream_t s) {
+    const int32_t nw = (int32_t)ceil_div(n, 32);
+    HCUDA(cudaMemsetAsync(bits_p, 0, sizeof(uint32_t) * nw, s));
+    HCUDA(cudaMemsetAsync(bits_t, 0, sizeof(uint32_t) * nw, s));
+    HCUDA(cudaMemsetAsync(c3, 0, sizeof(unsigned long long) * 3, s));
+    HCUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    if (n_pred > 0) launch(k_list_bits, grid_for(n_pred), 256, 0, s, d_pred, n_pred, n, bits_p, err);
+    if (n_truth > 0) launch(k_list_bits, grid_for(n_truth), 256, 0, s, d_truth, n_truth, n, bits_t, err);
+    launch(k_confusion, grid_for(nw), 256, 0, s, nw, (const uint32_t *)bits_p, (const uint32_t *)bits_t, c3);
+    launch(k_accuracy_ratios, 1, 32, 0, s, (const unsigned long long *)c3, r4);
+    HCUDA(cudaGetLastError());
+    unsigned long long h[3];
+    double r[4];
+    HCUDA(cudaMemcpyAsync(h, c3, sizeof(h), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaMemcpyAsync(r, r4, sizeof(r), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaMemcpyAsync(h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaStreamSynchronize(s));
+    h_out->tp = (int64_t)h[0];
+    h_out->fp = (int64_t)h[1];
+    h_out->fn = (int64_t)h[2];
+    h_out->jaccard = r[0];
+    h_out->precision = r[1];
+    h_out->recall = r[2];
+    h_out->f1 = r[3];
+}
+
 }  // namespace homln

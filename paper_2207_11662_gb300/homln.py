@@ -32,7 +32,7 @@ EXPORTS = [
     "homln_create", "homln_destroy", "homln_set_tuning", "homln_layer_closeness", "homln_and_aggregate",
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
-    "homln_version",
+    "homln_version", "homln_accuracy_noalloc",
 ]
 
 
@@ -102,6 +102,8 @@ def _load():
         "homln_sync": (S, [c_void_p]),
         "homln_last_error": (c_char_p, []),
         "homln_version": (c_char_p, []),
+        "homln_accuracy_noalloc": (S, [c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                                       POINTER(homln_accuracy_t)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -221,6 +223,15 @@ def homln_accuracy(h, pred, n_pred: int, truth, n_truth: int) -> dict:
     out = homln_accuracy_t()
     _check(lib.homln_accuracy(h, ptr(pred), int(n_pred), ptr(truth), int(n_truth), ctypes.byref(out)),
            "homln_accuracy")
+    return out.as_dict()
+
+
+def homln_accuracy_noalloc(n_nodes: int, pred, n_pred: int, truth, n_truth: int, stream=None) -> dict:
+    """Accuracy for callers that cannot allocate device memory: pred/truth must be device memory."""
+    out = homln_accuracy_t()
+    _check(lib.homln_accuracy_noalloc(int(n_nodes), ptr(pred), int(n_pred), ptr(truth), int(n_truth),
+                                      c_void_p(stream) if stream else None, ctypes.byref(out)),
+           "homln_accuracy_noalloc")
     return out.as_dict()
 
 
