@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--cpu-sample-sources", type=int, default=1500)
     p.add_argument("--words", type=int, default=0, help="BFS words per node (0 = auto)")
     p.add_argument("--alpha", type=int, default=0)
+    p.add_argument("--teams", type=int, default=0, help="BFS teams (0 = auto)")
     p.add_argument("--single-bfs", action="store_true",
                    help="profiling aid: build the workload, run one layer's all-sources BFS once, exit")
     p.add_argument("--launch-list", action="store_true",
@@ -182,6 +183,8 @@ def run_ours(args, rank, world, dist):
         tuning["words_per_node"] = args.words
     if args.alpha:
         tuning["push_alpha"] = args.alpha
+    if args.teams:
+        tuning["teams"] = args.teams
     sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
     stream = torch.cuda.current_stream(dev)
     dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
@@ -204,6 +207,7 @@ def run_ours(args, rank, world, dist):
                 R = torch.empty(n, dtype=torch.int32, device=dev)
                 cc = torch.empty(n, dtype=torch.float64, device=dev)
                 ids = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
+            H.homln_analyse(h, full, True)  # Psi of every layer and the AND graph in one launch
             outs = []
             for i in range(L):
                 H.homln_layer_closeness(h, i, F, R, cc)
@@ -318,7 +322,8 @@ def run_ours(args, rank, world, dist):
                                      for nm, a in zip(("naive", "cc1", "cc2"), accs)},
         "bfs_profile": {k: prof_count[k] for k in ("levels", "pull_levels", "push_levels", "batches",
                                                    "edges_scanned", "words_gathered", "edges_pushed",
-                                                   "words_pushed", "bytes", "visits", "words_per_node")},
+                                                   "words_pushed", "bytes", "visits", "words_per_node",
+                                                   "teams")},
     }
     result["value"] = round(work * world * args.steps / t_max / 1e9, 3)
     return result, net

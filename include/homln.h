@@ -119,7 +119,8 @@ typedef struct homln_tuning {
     int32_t threads;         /* threads per block of the persistent BFS (0 = 512) */
     int32_t blocks_per_sm;   /* resident blocks per SM (0 = as many as fit) */
     int32_t relabel;         /* 1 = degree-descending relabelling of each graph before BFS, 0 = off, -1 = default */
-    int32_t reserved[3];
+    int32_t teams;           /* teams of blocks that run (graph, source batch) tiles concurrently (0 = auto) */
+    int32_t reserved[2];
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.
@@ -153,6 +154,14 @@ HOMLN_API homln_status homln_set_tuning(homln_t h, const homln_tuning *t);
  *              connected layer this is Eq. 1, (n-1)/F. One correctly rounded division.
  * Any output may be NULL. Errors: EINVAL (layer out of range), ENOMEM, ECUDA, ETIMEOUT. */
 HOMLN_API homln_status homln_layer_closeness(homln_t h, int32_t layer, uint64_t *farness, uint32_t *reach, double *cc);
+
+/* Psi for several graphs in one persistent launch (Section 3: layers are analysed
+ * independently and in parallel): every layer in `layer_mask` not analysed yet and, if
+ * with_and != 0, the AND aggregate of `layer_mask`. The results are cached exactly as
+ * homln_layer_closeness / homln_and_closeness would cache them (and are identical); those
+ * calls then only copy them out. Asynchronous on the handle's stream.
+ * Errors: EINVAL (mask), ENOMEM, ECUDA; device errors surface at the next synchronising call. */
+HOMLN_API homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t with_and);
 
 /* Boolean AND aggregation of the layers in `layer_mask` (Section 3.1, Section 4 ground truth):
  * an edge is kept iff it is present in every selected layer. The AND graph is built
@@ -233,7 +242,7 @@ typedef struct homln_profile_t {
                                    lanes of one vertex counted once): the algorithmic bytes */
     int64_t visits;             /* vertex visits: non-skipped vertices processed, summed over levels */
     int32_t words_per_node;     /* W of the last instrumented launch */
-    int32_t reserved;
+    int32_t teams;              /* teams of the last instrumented launch */
 } homln_profile_t;
 
 HOMLN_API homln_status homln_set_profiling(homln_t h, int32_t timing, int32_t instrument);

@@ -8,6 +8,7 @@
 // aggregate of the selected layers, analysed the same way.
 #include "common.cuh"
 
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -179,12 +180,20 @@ struct DevOut {
     }
 };
 
-void analyse(homln_t h, GraphState &g) {
-    if (g.analysed) return;
+// Psi for every graph in `gs` that is not analysed yet, in one persistent BFS launch.
+void analyse_many(homln_t h, const std::vector<GraphState *> &gs) {
+    std::vector<GraphState *> todo;
+    for (GraphState *g : gs)
+        if (!g->analysed && std::find(todo.begin(), todo.end(), g) == todo.end()) todo.push_back(g);
+    if (todo.empty()) return;
     const int32_t n = h->n;
-    if (!g.F.alloc(&h->al, n) || !g.R.alloc(&h->al, n) || !g.cc.alloc(&h->al, n) || !g.sumdist.alloc(&h->al, n) ||
-        !g.deg.alloc(&h->al, n))
-        fail(HOMLN_ENOMEM, "closeness outputs");
+    std::vector<BfsJob> jobs;
+    for (GraphState *g : todo) {
+        if (!g->F.alloc(&h->al, n) || !g->R.alloc(&h->al, n) || !g->cc.alloc(&h->al, n) ||
+            !g->sumdist.alloc(&h->al, n) || !g->deg.alloc(&h->al, n))
+            fail(HOMLN_ENOMEM, "closeness outputs");
+        jobs.push_back(BfsJob{&g->csr, g->F.p, g->R.p});
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling) {
         HCUDA(cudaEventCreate(&e0));
@@ -192,8 +201,7 @@ void analyse(homln_t h, GraphState &g) {
         h->events.push_back({e0, e1});
     }
     BfsStats st;
-    msbfs_all_sources(g.csr, g.F.p, g.R.p, h->tuning, h->err.p, &h->al, h->stream, h->instrument ? &st : nullptr,
-                      nullptr, e0, e1);
+    msbfs_multi(jobs, h->tuning, h->err.p, &h->al, h->stream, h->instrument ? &st : nullptr, e0, e1);
     if (h->instrument) {
         h->stats.levels += st.levels;
         h->stats.pull_levels += st.pull_levels;
@@ -206,11 +214,16 @@ void analyse(homln_t h, GraphState &g) {
         h->stats.bytes += st.bytes;
         h->stats.visits += st.visits;
         h->stats.words_per_node = st.words_per_node;
+        h->stats.teams = st.teams;
     }
     h->bfs_launches += 1;
-    closeness_finalize(n, g.csr.rowptr.p, g.F.p, g.R.p, g.cc.p, g.sumdist.p, g.deg.p, h->stream);
-    g.analysed = true;
+    for (GraphState *g : todo) {
+        closeness_finalize(n, g->csr.rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p, g->deg.p, h->stream);
+        g->analysed = true;
+    }
 }
+
+void analyse(homln_t h, GraphState &g) { analyse_many(h, {&g}); }
 
 std::vector<int> mask_layers(homln_t h, uint64_t mask) {
     if (mask == 0) fail(HOMLN_EINVAL, "empty layer mask");
@@ -347,6 +360,8 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         if (t->blocks_per_sm < 0) fail(HOMLN_EINVAL, "blocks_per_sm must be >= 0");
         bt.blocks_per_sm = t->blocks_per_sm;
         if (t->relabel >= 0) bt.relabel = t->relabel ? 1 : 0;
+        if (t->teams < 0) fail(HOMLN_EINVAL, "teams must be >= 0");
+        bt.teams = t->teams;
     }
     h->tuning = bt;
     API_END
@@ -360,6 +375,17 @@ homln_status homln_layer_closeness(homln_t h, int32_t layer, uint64_t *farness, 
     GraphState &g = *h->layers[layer];
     analyse(h, g);
     write_closeness(h, g, farness, reach, cc);
+    API_END
+}
+
+homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t with_and) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    use_device(h);
+    std::vector<GraphState *> gs;
+    for (int i : mask_layers(h, layer_mask)) gs.push_back(h->layers[i].get());
+    if (with_and) gs.push_back(&and_graph(h, layer_mask));
+    analyse_many(h, gs);
     API_END
 }
 
@@ -535,7 +561,7 @@ homln_status homln_get_profile(homln_t h, homln_profile_t *out) {
     out->bytes = (int64_t)h->stats.bytes;
     out->visits = (int64_t)h->stats.visits;
     out->words_per_node = h->stats.words_per_node;
-    out->reserved = 0;
+    out->teams = h->stats.teams;
     API_END
 }
 

@@ -202,6 +202,7 @@ void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, c
 // ---------------------------------------------------------------------------
 struct BfsTuning {
     int W = 0;           // words per node (0 = auto)
+    int teams = 0;       // teams of blocks sharing the grid (0 = auto)
     int push_alpha = 8;
     int threads = 512;
     int blocks_per_sm = 0;
@@ -218,7 +219,18 @@ struct BfsStats {  // filled by an instrumented run
     uint64_t bytes = 0;        // bytes requested by the kernel's loads/stores (broadcast loads once)
     uint64_t visits = 0;       // vertex visits (non-quiet vertices processed per level)
     int words_per_node = 0;    // W of the last launch
+    int teams = 0;             // teams of the last launch
 };
+
+struct BfsJob {
+    const Csr *g;
+    uint64_t *F;
+    uint32_t *R;
+};
+
+// All-sources BFS of several graphs in one persistent launch (tiles = graph x source batch).
+void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
+                 BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop);
 
 // All-sources BFS: F[v] = sum of distances, R[v] = reachable count (v excluded).
 // ev_start/ev_stop (optional) are recorded on `s` right around the BFS kernel launch.

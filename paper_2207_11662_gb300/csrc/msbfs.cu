@@ -6,17 +6,21 @@
 //     F[v] = sum over vertices u reachable from v of d(v, u),
 //     R[v] = number of vertices reachable from v, v excluded.
 //
-// How: sources are processed in batches of S = 64*W. Every vertex carries three
-// S-bit words -- seen, frontier, next -- one bit per source of the batch. A
-// level either pulls (bottom-up: next[v] = OR of frontier[u] over neighbours u,
-// minus seen[v]) or pushes (top-down: every frontier vertex ORs its word into
-// its neighbours' accumulators, then a sweep keeps the bits not yet seen).
-// Because the graph is undirected, d(s, v) = d(v, s): a bit of source s that
-// first reaches v at level l adds l to F[v] directly, so no per-source scatter
-// is needed -- F[v] += l * popc(new[v]), R[v] += popc(new[v]).
+// How: sources are processed in batches of S = 64*W. Every vertex carries S-bit
+// words -- seen, frontier, next -- one bit per source of the batch. A level
+// either pulls (bottom-up: next[v] = OR of frontier[u] over neighbours u, minus
+// seen[v]) or pushes (top-down: every frontier vertex ORs its word into its
+// neighbours' accumulators, then a sweep keeps the bits not yet seen). Because
+// the graph is undirected, d(s, v) = d(v, s): a bit of source s that first
+// reaches v at level l adds l to F[v] directly, so no per-source scatter is
+// needed -- F[v] += l * popc(new[v]), R[v] += popc(new[v]).
 //
-// The whole BFS of a graph (every batch, every level) runs in one persistent
-// cooperative launch; levels are separated by a bounded grid barrier.
+// Scheduling: one persistent cooperative launch covers every (graph, batch)
+// tile of one or many graphs (the layers of a HoMLN and their AND aggregate, or
+// many HoMLNs). The grid is split into teams of blocks, interleaved over the
+// SMs; a team pops the next tile from a device queue and runs its levels,
+// separated by a bounded barrier over the team's blocks only. Teams progress
+// independently, so one team's wait overlaps another team's work.
 #include "common.cuh"
 
 #include <algorithm>
@@ -25,24 +29,53 @@ namespace homln {
 
 namespace {
 
-struct BfsArgs {
+struct GraphDesc {
+    const int64_t *rowptr;
+    const int32_t *col;
+    uint64_t *F;
+    uint32_t *R;
     int32_t n;
+    int32_t nbatches;
+    int32_t tile0;          // index of this graph's first tile
+    int32_t hub_block_end;  // vertices [0, hub_block_end) are handled by a whole block
+    int32_t hub_warp_end;   // vertices [hub_block_end, hub_warp_end) by a whole warp
+    int32_t pad;
+};
+
+struct TeamArgs {
+    const GraphDesc *graphs;
+    int32_t ngraphs;
+    int32_t ntiles;
+    int32_t nteams;
+    int32_t push_alpha;
+    int64_t maxn;               // per-team state stride in vertices
+    uint64_t *state;            // [4 arrays][nteams][maxn * W]: seen, frontier A, frontier B, accumulator
+    uint8_t *quiet;             // [nteams][maxn]
+    unsigned long long *ctr;    // [nteams][16]: 3 counter slots x {new bits, frontier edges, unfinished edges}
+    uint32_t *bar;              // [nteams][32]: count, generation, ..., [8] current tile
+    int32_t *queue;             // next tile to hand out
+    int32_t *err;
+    int32_t atomic_fr;          // several teams may update one graph's F/R
+    unsigned long long *stats;
+};
+
+// One tile as seen by one block: the graph, the team's state, the block's place in the team.
+struct Tile {
     const int64_t *__restrict__ rowptr;
     const int32_t *__restrict__ col;
     uint64_t *seen;
-    uint64_t *fa;
-    uint64_t *fb;
-    uint64_t *acc;     // top-down accumulator; all zero between phases
-    uint8_t *quiet;    // per vertex: levels since its seen word became full (saturates at 2)
+    uint64_t *acc;
+    uint8_t *quiet;
     uint64_t *F;
     uint32_t *R;
-    unsigned long long *ctr;  // 3 slots x {new bits, frontier edges, unfinished edges, spare}
-    GridBarrier bar;
-    int32_t nbatches;
+    unsigned long long *ctr;
+    int32_t n;
+    int32_t hub_block_end;
+    int32_t hub_warp_end;
+    int32_t rank;   // block index within the team
+    int32_t tsize;  // blocks in the team
     int32_t push_alpha;
-    int32_t hub_block_end;  // vertices [0, hub_block_end) are pulled/pushed by a whole block
-    int32_t hub_warp_end;   // vertices [hub_block_end, hub_warp_end) by a whole warp
-    unsigned long long *stats;
+    bool atomic_fr;
 };
 
 // A vertex is "quiet" once its seen word has been full at the start of two levels: both
@@ -110,27 +143,90 @@ __device__ __forceinline__ bool covers(const uint64_t (&acc)[K], const uint64_t 
     return ok;
 }
 
+// Bounded barrier over the blocks of one team (all co-resident in a cooperative launch).
+struct TeamBarrier {
+    uint32_t *count;
+    uint32_t *gen;
+    int32_t *err;
+    uint32_t size;
+};
+
+__device__ __forceinline__ bool team_sync(const TeamBarrier &b, uint64_t limit_ns = 2000000000ull) {
+    if (b.size == 1) {
+        __syncthreads();
+        return *(volatile int32_t *)b.err == 0;
+    }
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint32_t g = ld_acquire_u32(b.gen);
+        __threadfence();
+        uint32_t arrived = atomicAdd(b.count, 1u);
+        if (arrived == b.size - 1) {
+            *b.count = 0;
+            __threadfence();
+            st_release_u32(b.gen, g + 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_u32(b.gen) == g) {
+                if ((++spins & 255u) == 0) {
+                    if (globaltimer_ns() - t0 > limit_ns) {
+                        dev_fail(b.err, DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (*(volatile int32_t *)b.err != 0) {
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int32_t *)b.err != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // OR the frontier words (this lane's K of them) of neighbours rb+p, rb+p+S, ... into acc;
-// stop once every bit this lane still needs is present. Returns the neighbours visited.
+// stop once every bit this lane still needs is present. The next four column indices
+// are loaded while the current four frontier words are in flight. Returns neighbours visited.
 template <int W>
-__device__ __forceinline__ int64_t gather_or(const BfsArgs &a, const uint64_t *__restrict__ cur, int64_t rb,
-                                             int64_t re, int p, int S, int q,
-                                             const uint64_t (&need)[Geo<W>::K], uint64_t (&acc)[Geo<W>::K]) {
+__device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__restrict__ cur, int64_t rb, int64_t re,
+                                             int p, int S, int q, const uint64_t (&need)[Geo<W>::K],
+                                             uint64_t (&acc)[Geo<W>::K]) {
     constexpr int K = Geo<W>::K;
+    const int64_t S4 = 4 * (int64_t)S;
     int64_t j = rb + p;
     int64_t it = 0;
-    for (; j + 3 * (int64_t)S < re; j += 4 * (int64_t)S) {
-        const int32_t u0 = __ldg(a.col + j), u1 = __ldg(a.col + j + S), u2 = __ldg(a.col + j + 2 * S),
-                      u3 = __ldg(a.col + j + 3 * S);
-        uint64_t f0[K], f1[K], f2[K], f3[K];
-        ldw<K>(cur + (int64_t)u0 * W + q * K, f0);
-        ldw<K>(cur + (int64_t)u1 * W + q * K, f1);
-        ldw<K>(cur + (int64_t)u2 * W + q * K, f2);
-        ldw<K>(cur + (int64_t)u3 * W + q * K, f3);
+    if (j + 3 * (int64_t)S < re) {
+        int32_t u0 = __ldg(a.col + j), u1 = __ldg(a.col + j + S), u2 = __ldg(a.col + j + 2 * S),
+                u3 = __ldg(a.col + j + 3 * S);
+        while (true) {
+            uint64_t f0[K], f1[K], f2[K], f3[K];
+            ldw<K>(cur + (int64_t)u0 * W + q * K, f0);
+            ldw<K>(cur + (int64_t)u1 * W + q * K, f1);
+            ldw<K>(cur + (int64_t)u2 * W + q * K, f2);
+            ldw<K>(cur + (int64_t)u3 * W + q * K, f3);
+            const int64_t jn = j + S4;
+            const bool more = jn + 3 * (int64_t)S < re;
+            if (more) {
+                u0 = __ldg(a.col + jn);
+                u1 = __ldg(a.col + jn + S);
+                u2 = __ldg(a.col + jn + 2 * S);
+                u3 = __ldg(a.col + jn + 3 * S);
+            }
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] |= f0[k] | f1[k] | f2[k] | f3[k];
-        it += 4;
-        if (covers<K>(acc, need)) return it;
+            for (int k = 0; k < K; ++k) acc[k] |= f0[k] | f1[k] | f2[k] | f3[k];
+            it += 4;
+            j = jn;
+            if (covers<K>(acc, need)) return it;
+            if (!more) break;
+        }
     }
     for (; j < re; j += S) {
         const int32_t u = __ldg(a.col + j);
@@ -148,8 +244,8 @@ struct PhaseCounters {
     unsigned long long newbits = 0, mf = 0, mu = 0;
 };
 
-// Block-reduce the phase counters and add them to the slot of this producing phase.
-__device__ __forceinline__ void flush_counters(const BfsArgs &a, PhaseCounters &c, uint32_t ps) {
+// Block-reduce the phase counters and add them to the team's slot of this producing phase.
+__device__ __forceinline__ void flush_counters(const Tile &a, PhaseCounters &c, uint32_t ps) {
     __shared__ unsigned long long red[3][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     unsigned long long x0 = warp_sum(c.newbits), x1 = warp_sum(c.mf), x2 = warp_sum(c.mu);
@@ -174,8 +270,8 @@ __device__ __forceinline__ void flush_counters(const BfsArgs &a, PhaseCounters &
     c = PhaseCounters{};
 }
 
-__device__ __forceinline__ void reset_next_slot(const BfsArgs &a, uint32_t ps) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void reset_next_slot(const Tile &a, uint32_t ps) {
+    if (a.rank == 0 && threadIdx.x == 0) {
         unsigned long long *slot = a.ctr + 4 * ((ps + 1) % 3);
         slot[0] = 0;
         slot[1] = 0;
@@ -186,7 +282,7 @@ __device__ __forceinline__ void reset_next_slot(const BfsArgs &a, uint32_t ps) {
 // Record the new bits of v (already reduced to this lane's K words) and its counters.
 // full0: the vertex's seen word was already full when the level started (its new bits are 0).
 template <int W, bool STATS>
-__device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool writer, int64_t v, int q,
+__device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writer, int64_t v, int q,
                                               const uint64_t (&s)[Geo<W>::K], const uint64_t (&nw)[Geo<W>::K],
                                               uint64_t *nxt, int level, int64_t deg, bool full0, uint8_t qv,
                                               PhaseCounters &c, unsigned long long *st) {
@@ -207,11 +303,16 @@ __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool w
         if (STATS) st[ST_BYTES] += (any ? 16 : 8) * K;
     }
     cnt = group_sum<T>(cnt);
-    bool gfull = !group_any<T>(!full);
+    const bool gfull = !group_any<T>(!full);
     if (act && writer && q == 0) {
         if (cnt) {
-            a.F[v] += (uint64_t)level * cnt;
-            a.R[v] += cnt;
+            if (a.atomic_fr) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.F + v), (unsigned long long)level * cnt);
+                atomicAdd(a.R + v, cnt);
+            } else {
+                a.F[v] += (uint64_t)level * cnt;
+                a.R[v] += cnt;
+            }
             c.newbits += cnt;
             c.mf += (unsigned long long)deg;
             if (STATS) st[ST_BYTES] += 24;
@@ -227,9 +328,9 @@ __device__ __forceinline__ void commit_vertex(const BfsArgs &a, bool act, bool w
 // Level 0 and 1 of a batch: seen = own source bit (plus padding bits for a short
 // last batch); every source ORs its bit into its neighbours' accumulators.
 template <int W, bool STATS>
-__device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns, unsigned long long *st) {
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void phase_start_batch(const Tile &a, int32_t s0, int32_t ns, unsigned long long *st) {
+    const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
+    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
         const int64_t v = i / W;
         const int wi = (int)(i % W);
@@ -260,13 +361,13 @@ __device__ void phase_start_batch(const BfsArgs &a, int32_t s0, int32_t ns, unsi
 
 // Keep the accumulated bits not yet seen: they become the next frontier.
 template <int W, bool STATS>
-__device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c,
+__device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c,
                                unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     reset_next_slot(a, ps);
     const int lane = threadIdx.x & 31, q = lane % T;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t G = ((int64_t)gridDim.x * blockDim.x) / T;
+    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
+    const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
     for (int64_t v = gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
         uint8_t qv = 0;
         if (v < a.n) {
@@ -306,7 +407,7 @@ __device__ void phase_finalize(const BfsArgs &a, uint64_t *nxt, int level, uint3
 
 // Bottom-up level: each vertex still missing bits gathers its neighbours' frontier words.
 template <int W, bool STATS>
-__device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, uint64_t *nxt, int level, uint32_t ps,
+__device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint64_t *nxt, int level, uint32_t ps,
                            PhaseCounters &c, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     reset_next_slot(a, ps);
@@ -317,7 +418,7 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
     {
         __shared__ uint64_t red[32][16][2];
         const int S = blockDim.x / T, p = threadIdx.x / T;
-        for (int64_t v = blockIdx.x; v < a.hub_block_end; v += gridDim.x) {
+        for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) {
             const uint8_t qv = a.quiet[v];
             if (STATS && threadIdx.x == 0) st[ST_BYTES] += 1;
             if (qv >= QUIET) continue;  // uniform over the block
@@ -367,8 +468,8 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
     // --- warp tier: hubs below the block threshold, all slots of a warp share one row
     {
         const int S = 32 / T, p = lane / T;
-        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const int64_t NW = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
+        const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
         for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) {
             const uint8_t qv = a.quiet[v];
             if (STATS && lane == 0) st[ST_BYTES] += 1;
@@ -404,8 +505,8 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
     }
     // --- group tier: T lanes per vertex
     {
-        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        const int64_t G = ((int64_t)gridDim.x * blockDim.x) / T;
+        const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
+        const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
         for (int64_t v = a.hub_warp_end + gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
             uint8_t qv = 0;
             if (v < a.n) {
@@ -451,7 +552,7 @@ __device__ void phase_pull(const BfsArgs &a, const uint64_t *__restrict__ cur, u
 // Top-down level: frontier vertices OR their words into the neighbours' accumulators
 // (quiet neighbours are full and are skipped).
 template <int W, bool STATS>
-__device__ void phase_push(const BfsArgs &a, const uint64_t *__restrict__ cur, unsigned long long *st) {
+__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
@@ -477,63 +578,114 @@ __device__ void phase_push(const BfsArgs &a, const uint64_t *__restrict__ cur, u
                 }
         }
     };
-    for (int64_t v = blockIdx.x; v < a.hub_block_end; v += gridDim.x) push_row(v, threadIdx.x / T, blockDim.x / T);
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t NW = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) push_row(v, threadIdx.x / T, blockDim.x / T);
+    const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
     for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) push_row(v, lane / T, 32 / T);
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t G = ((int64_t)gridDim.x * blockDim.x) / T;
+    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
+    const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
     for (int64_t v = a.hub_warp_end + gtid / T; v < a.n; v += G) push_row(v, 0, 1);
 }
 
+// The levels of one batch (sources s0 .. s0+ns-1) of one graph, run by one team.
+// Returns false if a barrier gave up (the kernel must stop).
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512, 2) k_msbfs(BfsArgs a) {
+__device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamBarrier &tb, int32_t s0, int32_t ns,
+                          uint32_t &ps, PhaseCounters &c, unsigned long long *st) {
+    phase_start_batch<W, STATS>(a, s0, ns, st);
+    if (!team_sync(tb)) return false;
+    phase_finalize<W, STATS>(a, fa, 1, ps, c, st);
+    ++ps;
+    if (!team_sync(tb)) return false;
+    uint64_t *cur = fa, *nxt = fb;
+    if (STATS) { st[ST_BATCHES] += 1; st[ST_LEVELS] += 1; st[ST_PUSH] += 1; }
+    for (int level = 2; level <= a.n + 1; ++level) {
+        const unsigned long long *slot = a.ctr + 4 * ((ps - 1) % 3);
+        const unsigned long long newbits = __ldcg(slot), mf = __ldcg(slot + 1), mu = __ldcg(slot + 2);
+        if (newbits == 0) break;
+        const bool push = (unsigned long long)a.push_alpha * mf < mu;
+        if (push) {
+            phase_push<W, STATS>(a, cur, st);
+            if (!team_sync(tb)) return false;
+            phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
+        } else {
+            phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st);
+        }
+        ++ps;
+        if (!team_sync(tb)) return false;
+        if (STATS) { st[ST_LEVELS] += 1; st[push ? ST_PUSH : ST_PULL] += 1; }
+        uint64_t *t = cur; cur = nxt; nxt = t;
+    }
+    return true;
+}
+
+template <int W, bool STATS>
+__global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
     PhaseCounters c;
     unsigned long long st[ST_N];
 #pragma unroll
     for (int i = 0; i < ST_N; ++i) st[i] = 0;
-    uint32_t ps = 0;  // index of the next counter-producing phase
-    for (int32_t b = 0; b < a.nbatches; ++b) {
+    const int team = (int)(blockIdx.x % (unsigned)A.nteams);
+    const int rank = (int)(blockIdx.x / (unsigned)A.nteams);
+    const int tsize = (int)(gridDim.x / (unsigned)A.nteams);
+    uint32_t *tbar = A.bar + (size_t)team * 32;
+    const TeamBarrier tb{tbar, tbar + 1, A.err, (uint32_t)tsize};
+    const size_t stride = (size_t)A.maxn * W;
+    const size_t arr = stride * A.nteams;
+    uint64_t *seen = A.state + 0 * arr + team * stride;
+    uint64_t *fa = A.state + 1 * arr + team * stride;
+    uint64_t *fb = A.state + 2 * arr + team * stride;
+    uint64_t *acc = A.state + 3 * arr + team * stride;
+    uint8_t *quiet = A.quiet + (size_t)team * A.maxn;
+    unsigned long long *ctr = A.ctr + (size_t)team * 16;
+    volatile int32_t *tile_slot = reinterpret_cast<volatile int32_t *>(tbar + 8);
+    uint32_t ps = 0;
+    bool ok = true;
+    while (ok) {
+        if (rank == 0 && threadIdx.x == 0) *tile_slot = atomicAdd(A.queue, 1);
+        if (!team_sync(tb)) break;
+        const int32_t t = *tile_slot;
+        if (t >= A.ntiles) break;
+        int lo = 0, hi = A.ngraphs;  // the graph whose tiles contain t
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (A.graphs[mid].tile0 <= t) lo = mid; else hi = mid;
+        }
+        const GraphDesc &g = A.graphs[lo];
+        Tile a;
+        a.rowptr = g.rowptr;
+        a.col = g.col;
+        a.seen = seen;
+        a.acc = acc;
+        a.quiet = quiet;
+        a.F = g.F;
+        a.R = g.R;
+        a.ctr = ctr;
+        a.n = g.n;
+        a.hub_block_end = g.hub_block_end;
+        a.hub_warp_end = g.hub_warp_end;
+        a.rank = rank;
+        a.tsize = tsize;
+        a.push_alpha = A.push_alpha;
+        a.atomic_fr = A.atomic_fr != 0;
+        const int32_t b = t - g.tile0;
         const int32_t s0 = b * 64 * W;
-        const int32_t ns = min(64 * W, a.n - s0);
-        phase_start_batch<W, STATS>(a, s0, ns, st);
-        if (!grid_sync(a.bar)) return;
-        phase_finalize<W, STATS>(a, a.fa, 1, ps, c, st);
-        ++ps;
-        if (!grid_sync(a.bar)) return;
-        uint64_t *cur = a.fa, *nxt = a.fb;
-        if (STATS) { st[ST_BATCHES] += 1; st[ST_LEVELS] += 1; st[ST_PUSH] += 1; }
-        for (int level = 2; level <= a.n + 1; ++level) {
-            const unsigned long long *slot = a.ctr + 4 * ((ps - 1) % 3);
-            const unsigned long long newbits = __ldcg(slot), mf = __ldcg(slot + 1), mu = __ldcg(slot + 2);
-            if (newbits == 0) break;
-            const bool push = (unsigned long long)a.push_alpha * mf < mu;
-            if (push) {
-                phase_push<W, STATS>(a, cur, st);
-                if (!grid_sync(a.bar)) return;
-                phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
-            } else {
-                phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st);
-            }
-            ++ps;
-            if (!grid_sync(a.bar)) return;
-            if (STATS) { st[ST_LEVELS] += 1; st[push ? ST_PUSH : ST_PULL] += 1; }
-            uint64_t *t = cur; cur = nxt; nxt = t;
-        }
+        const int32_t ns = min(64 * W, g.n - s0);
+        ok = run_batch<W, STATS>(a, fa, fb, tb, s0, ns, ps, c, st);
     }
-    if (STATS && a.stats) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) {
-            atomicAdd(a.stats + ST_LEVELS, st[ST_LEVELS]);
-            atomicAdd(a.stats + ST_PULL, st[ST_PULL]);
-            atomicAdd(a.stats + ST_PUSH, st[ST_PUSH]);
-            atomicAdd(a.stats + ST_BATCHES, st[ST_BATCHES]);
+    if (STATS && A.stats) {
+        if (threadIdx.x == 0 && rank == 0) {
+            atomicAdd(A.stats + ST_LEVELS, st[ST_LEVELS]);
+            atomicAdd(A.stats + ST_PULL, st[ST_PULL]);
+            atomicAdd(A.stats + ST_PUSH, st[ST_PUSH]);
+            atomicAdd(A.stats + ST_BATCHES, st[ST_BATCHES]);
         }
-        atomicAdd(a.stats + ST_EDGES, st[ST_EDGES]);
-        atomicAdd(a.stats + ST_WORDS, st[ST_WORDS]);
-        atomicAdd(a.stats + ST_PUSHED, st[ST_PUSHED]);
-        atomicAdd(a.stats + ST_PUSHWORDS, st[ST_PUSHWORDS]);
-        atomicAdd(a.stats + ST_BYTES, st[ST_BYTES]);
-        atomicAdd(a.stats + ST_VISITS, st[ST_VISITS]);
+        atomicAdd(A.stats + ST_EDGES, st[ST_EDGES]);
+        atomicAdd(A.stats + ST_WORDS, st[ST_WORDS]);
+        atomicAdd(A.stats + ST_PUSHED, st[ST_PUSHED]);
+        atomicAdd(A.stats + ST_PUSHWORDS, st[ST_PUSHWORDS]);
+        atomicAdd(A.stats + ST_BYTES, st[ST_BYTES]);
+        atomicAdd(A.stats + ST_VISITS, st[ST_VISITS]);
     }
 }
 
@@ -557,7 +709,7 @@ __global__ void k_tier_bounds(int32_t n, const int64_t *__restrict__ rp, int64_t
     }
 }
 
-typedef void (*BfsKernel)(BfsArgs);
+typedef void (*BfsKernel)(TeamArgs);
 
 template <int W>
 BfsKernel pick_kernel(bool stats) {
@@ -576,69 +728,48 @@ BfsKernel kernel_for(int W, bool stats) {
     }
 }
 
+// Bytes of BFS state across all teams. Measured on the 50,000-node power-law workload:
+// 8 teams x W=8 and 4 teams x W=16 (both 102 MB) beat every 51 MB split, so the budget
+// lets the state exceed L2 a little; the frontier gathers still mostly hit in L2.
+constexpr double kStateBudget = 104.0e6;
+constexpr int kDefaultTeams = 8;
+
 }  // namespace
 
 int msbfs_pick_words(int32_t n, int64_t nnz) {
     (void)nnz;
-    // four n x W word arrays should stay well inside L2 (about 48 MB of it)
     int W = 32;
-    while (W > 1 && 4.0 * n * 8.0 * W > 48.0e6) W >>= 1;
+    while (W > 1 && 4.0 * n * 8.0 * W > kStateBudget) W >>= 1;
     while (W > 1 && (int64_t)64 * (W / 2) >= n) W >>= 1;  // no wider than the node count needs
     return W;
 }
 
-void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuning &t, int32_t *d_err, Alloc *al,
-                       cudaStream_t s, BfsStats *stats, float *kernel_ms, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
-    const int32_t n = g.n;
-    if (n <= 0) return;
-    const int W = t.W > 0 ? t.W : msbfs_pick_words(n, g.nnz);
-    const int T = W >= 2 ? W / 2 : 1;
+void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
+                 BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    if (jobs.empty()) return;
+    int32_t maxn = 0;
+    int64_t maxnnz = 0;
+    for (const BfsJob &j : jobs) {
+        maxn = std::max(maxn, j.g->n);
+        maxnnz = std::max(maxnnz, j.g->nnz);
+    }
+    if (maxn <= 0) return;
     const int threads = t.threads > 0 ? t.threads : 512;
     if (threads % 32 != 0 || threads > 512 || threads < 64) fail(HOMLN_EINVAL, "threads must be 64..512, multiple of 32");
 
-    const Csr *G = &g;
-    Csr rl;
-    DBuf<int32_t> perm;
-    if (t.relabel) {
-        relabel_by_degree(g, rl, perm, al, s);
-        G = &rl;
+    // teams and words per node: every team keeps its own state, and all of it should fit the budget
+    int nteams = t.teams > 0 ? t.teams : kDefaultTeams;
+    int W = t.W;
+    if (W <= 0) {
+        W = msbfs_pick_words(maxn, maxnnz);
+        while (W > 1 && nteams * 4.0 * maxn * 8.0 * W > kStateBudget) W >>= 1;
     }
-    const size_t words = (size_t)n * W;
-    DBuf<uint64_t> seen, fa, fb, acc, Fi;
-    DBuf<uint8_t> quiet;
-    DBuf<uint32_t> Ri;
-    DBuf<unsigned long long> ctr, st;
-    DBuf<uint32_t> barmem;
-    DBuf<int32_t> tiers;
-    if (!seen.alloc(al, words) || !fa.alloc(al, words) || !fb.alloc(al, words) || !acc.alloc(al, words) ||
-        !quiet.alloc(al, (size_t)n) ||
-        !ctr.alloc(al, 12) || !barmem.alloc(al, 2) || !tiers.alloc(al, 2))
-        fail(HOMLN_ENOMEM, "bfs state");
-    uint64_t *F = d_F;
-    uint32_t *R = d_R;
-    if (t.relabel) {
-        if (!Fi.alloc(al, n) || !Ri.alloc(al, n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
-        F = Fi.p;
-        R = Ri.p;
+    if (t.teams <= 0) {  // no more teams than tiles
+        int64_t tiles = 0;
+        for (const BfsJob &j : jobs) tiles += ceil_div(j.g->n, 64 * W);
+        if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
     }
-    if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
-    HCUDA(cudaMemsetAsync(acc.p, 0, words * sizeof(uint64_t), s));
-    HCUDA(cudaMemsetAsync(F, 0, (size_t)n * sizeof(uint64_t), s));
-    HCUDA(cudaMemsetAsync(R, 0, (size_t)n * sizeof(uint32_t), s));
-    HCUDA(cudaMemsetAsync(ctr.p, 0, 12 * sizeof(unsigned long long), s));
-    HCUDA(cudaMemsetAsync(barmem.p, 0, 2 * sizeof(uint32_t), s));
-    HCUDA(cudaMemsetAsync(tiers.p, 0, 2 * sizeof(int32_t), s));
-    if (stats) HCUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
-
-    int32_t h_tiers[2] = {0, 0};
-    if (t.relabel && G->nnz > 0) {
-        const int64_t slots_block = threads / T, slots_warp = 32 / T;
-        launch(k_tier_bounds, (unsigned)ceil_div(n, 256), 256, 0, s, n, G->rowptr.p, 32 * slots_block, 16 * slots_warp,
-                                                               tiers.p);
-        HCUDA(cudaMemcpyAsync(h_tiers, tiers.p, sizeof(h_tiers), cudaMemcpyDeviceToHost, s));
-        HCUDA(cudaStreamSynchronize(s));
-        if (h_tiers[1] < h_tiers[0]) h_tiers[1] = h_tiers[0];
-    }
+    const int T = W >= 2 ? W / 2 : 1;
 
     BfsKernel kern = kernel_for(W, stats != nullptr);
     int dev = 0, nsm = 0, coop = 0, per_sm = 0;
@@ -649,46 +780,97 @@ void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuni
     HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
+    int grid = nsm * per_sm;
+    if (nteams > grid) nteams = grid;
+    grid -= grid % nteams;
 
-    BfsArgs a{};
-    a.n = n;
-    a.rowptr = G->rowptr.p;
-    a.col = G->col.p;
-    a.seen = seen.p;
-    a.fa = fa.p;
-    a.fb = fb.p;
-    a.acc = acc.p;
-    a.quiet = quiet.p;
-    a.F = F;
-    a.R = R;
-    a.ctr = ctr.p;
-    a.bar = GridBarrier{barmem.p, barmem.p + 1, d_err};
-    a.nbatches = (int32_t)ceil_div(n, 64 * W);
-    a.push_alpha = t.push_alpha > 0 ? t.push_alpha : 8;
-    a.hub_block_end = h_tiers[0];
-    a.hub_warp_end = h_tiers[1];
-    a.stats = stats ? st.p : nullptr;
-    void *args[] = {&a};
-
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (kernel_ms) {
-        HCUDA(cudaEventCreate(&e0));
-        HCUDA(cudaEventCreate(&e1));
-        HCUDA(cudaEventRecord(e0, s));
+    // relabel each graph by degree and find its hub tiers
+    const size_t ng = jobs.size();
+    std::vector<Csr> rl(ng);
+    std::vector<DBuf<int32_t>> perm(ng);
+    std::vector<DBuf<uint64_t>> Fi(ng);
+    std::vector<DBuf<uint32_t>> Ri(ng);
+    std::vector<GraphDesc> desc(ng);
+    DBuf<int32_t> tiers;
+    if (!tiers.alloc(al, 2 * ng)) fail(HOMLN_ENOMEM, "bfs tiers");
+    HCUDA(cudaMemsetAsync(tiers.p, 0, 2 * ng * sizeof(int32_t), s));
+    const int64_t slots_block = threads / T, slots_warp = 32 / T;
+    int32_t tile = 0;
+    for (size_t i = 0; i < ng; ++i) {
+        const Csr *G = jobs[i].g;
+        GraphDesc &d = desc[i];
+        d.n = G->n;
+        d.nbatches = (int32_t)ceil_div(G->n, 64 * W);
+        d.tile0 = tile;
+        tile += d.nbatches;
+        if (t.relabel) {
+            relabel_by_degree(*G, rl[i], perm[i], al, s);
+            if (!Fi[i].alloc(al, G->n) || !Ri[i].alloc(al, G->n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
+            G = &rl[i];
+            d.F = Fi[i].p;
+            d.R = Ri[i].p;
+            if (G->nnz > 0)
+                launch(k_tier_bounds, (unsigned)ceil_div(G->n, 256), 256, 0, s, G->n, G->rowptr.p, 4 * slots_block,
+                       4 * slots_warp, tiers.p + 2 * i);
+        } else {
+            d.F = jobs[i].F;
+            d.R = jobs[i].R;
+        }
+        d.rowptr = G->rowptr.p;
+        d.col = G->col.p;
+        HCUDA(cudaMemsetAsync(d.F, 0, (size_t)G->n * sizeof(uint64_t), s));
+        HCUDA(cudaMemsetAsync(d.R, 0, (size_t)G->n * sizeof(uint32_t), s));
     }
+    std::vector<int32_t> h_tiers(2 * ng, 0);
+    HCUDA(cudaMemcpyAsync(h_tiers.data(), tiers.p, 2 * ng * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ng; ++i) {
+        desc[i].hub_block_end = h_tiers[2 * i];
+        desc[i].hub_warp_end = std::max(h_tiers[2 * i + 1], h_tiers[2 * i]);
+    }
+
+    const size_t words = (size_t)maxn * W * nteams;
+    DBuf<uint64_t> state;
+    DBuf<uint8_t> quiet;
+    DBuf<unsigned long long> ctr, st;
+    DBuf<uint32_t> barmem;
+    DBuf<int32_t> queue;
+    DBuf<GraphDesc> d_desc;
+    if (!state.alloc(al, 4 * words) || !quiet.alloc(al, (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
+        !barmem.alloc(al, 32 * nteams) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
+        fail(HOMLN_ENOMEM, "bfs state");
+    if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
+    HCUDA(cudaMemsetAsync(state.p + 3 * words, 0, words * sizeof(uint64_t), s));  // accumulators
+    HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
+    HCUDA(cudaMemsetAsync(barmem.p, 0, 32 * nteams * sizeof(uint32_t), s));
+    HCUDA(cudaMemsetAsync(queue.p, 0, sizeof(int32_t), s));
+    HCUDA(cudaMemcpyAsync(d_desc.p, desc.data(), ng * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
+    if (stats) HCUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
+
+    TeamArgs A{};
+    A.graphs = d_desc.p;
+    A.ngraphs = (int32_t)ng;
+    A.ntiles = tile;
+    A.nteams = nteams;
+    A.push_alpha = t.push_alpha > 0 ? t.push_alpha : 8;
+    A.maxn = maxn;
+    A.state = state.p;
+    A.quiet = quiet.p;
+    A.ctr = ctr.p;
+    A.bar = barmem.p;
+    A.queue = queue.p;
+    A.err = d_err;
+    A.atomic_fr = nteams > 1 ? 1 : 0;
+    A.stats = stats ? st.p : nullptr;
+    void *args[] = {&A};
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(nsm * per_sm), dim3(threads), args, 0, s));
+    HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
     if (ev_stop) HCUDA(cudaEventRecord(ev_stop, s));
-    if (kernel_ms) {
-        HCUDA(cudaEventRecord(e1, s));
-        HCUDA(cudaEventSynchronize(e1));
-        HCUDA(cudaEventElapsedTime(kernel_ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
     if (t.relabel)
-        launch(k_scatter_back, (unsigned)ceil_div(n, 256), 256, 0, s, n, perm.p, Fi.p, Ri.p, d_F, d_R);
+        for (size_t i = 0; i < ng; ++i)
+            launch(k_scatter_back, (unsigned)ceil_div(desc[i].n, 256), 256, 0, s, desc[i].n, perm[i].p, Fi[i].p,
+                   Ri[i].p, jobs[i].F, jobs[i].R);
     HCUDA(cudaGetLastError());
     if (stats) {
         unsigned long long h[ST_N];
@@ -704,8 +886,16 @@ void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuni
         stats->push_words += h[ST_PUSHWORDS];
         stats->bytes += h[ST_BYTES];
         stats->visits += h[ST_VISITS];
+        stats->words_per_node = W;
+        stats->teams = nteams;
     }
-    if (stats) stats->words_per_node = W;
+}
+
+void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuning &t, int32_t *d_err, Alloc *al,
+                       cudaStream_t s, BfsStats *stats, float *kernel_ms, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    (void)kernel_ms;
+    std::vector<BfsJob> jobs{BfsJob{&g, d_F, d_R}};
+    msbfs_multi(jobs, t, d_err, al, s, stats, ev_start, ev_stop);
 }
 
 }  // namespace homln

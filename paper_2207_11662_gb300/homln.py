@@ -32,7 +32,7 @@ EXPORTS = [
     "homln_create", "homln_destroy", "homln_set_tuning", "homln_layer_closeness", "homln_and_aggregate",
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
-    "homln_version", "homln_accuracy_noalloc",
+    "homln_version", "homln_accuracy_noalloc", "homln_analyse",
 ]
 
 
@@ -51,7 +51,7 @@ class homln_accuracy_t(ctypes.Structure):
 
 class homln_tuning(ctypes.Structure):
     _fields_ = [("words_per_node", c_int32), ("push_alpha", c_int32), ("threads", c_int32),
-                ("blocks_per_sm", c_int32), ("relabel", c_int32), ("reserved", c_int32 * 3)]
+                ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("reserved", c_int32 * 2)]
 
 
 class homln_profile_t(ctypes.Structure):
@@ -59,7 +59,7 @@ class homln_profile_t(ctypes.Structure):
                 ("levels", c_int64), ("pull_levels", c_int64), ("push_levels", c_int64), ("batches", c_int64),
                 ("edges_scanned", c_int64), ("words_gathered", c_int64), ("edges_pushed", c_int64),
                 ("words_pushed", c_int64), ("bytes", c_int64), ("visits", c_int64), ("words_per_node", c_int32),
-                ("reserved", c_int32)]
+                ("teams", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +90,7 @@ def _load():
         "homln_destroy": (S, [c_void_p]),
         "homln_set_tuning": (S, [c_void_p, POINTER(homln_tuning)]),
         "homln_layer_closeness": (S, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+        "homln_analyse": (S, [c_void_p, c_uint64, c_int32]),
         "homln_and_aggregate": (S, [c_void_p, c_uint64, c_int64, c_void_p, c_void_p, POINTER(c_int64)]),
         "homln_and_closeness": (S, [c_void_p, c_uint64, c_void_p, c_void_p, c_void_p]),
         "homln_topk": (S, [c_void_p, c_int32, c_uint64, POINTER(homln_select), c_void_p, POINTER(c_int32)]),
@@ -185,9 +186,13 @@ def homln_destroy(h) -> None:
     _check(lib.homln_destroy(h), "homln_destroy")
 
 
-def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1) -> None:
-    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel)
+def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0) -> None:
+    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams)
     _check(lib.homln_set_tuning(h, ctypes.byref(t)), "homln_set_tuning")
+
+
+def homln_analyse(h, layer_mask: int, with_and: bool = True) -> None:
+    _check(lib.homln_analyse(h, int(layer_mask), int(bool(with_and))), "homln_analyse")
 
 
 def homln_layer_closeness(h, layer: int, farness=None, reach=None, cc=None) -> None:
@@ -285,6 +290,9 @@ class Network:
 
     def _empty(self, count, dtype):
         return self.torch.empty(max(int(count), 1), dtype=dtype, device=self.device)
+
+    def analyse(self, mask: int, with_and: bool = True):
+        homln_analyse(self.h, mask, with_and)
 
     def layer_closeness(self, layer: int):
         F, R, cc = self._empty(self.n, self.torch.int64), self._empty(self.n, self.torch.int32), \

@@ -116,6 +116,19 @@ def test_push_pull_extremes(H, alpha):
     full_parity(H, net, sel, tuning=dict(push_alpha=alpha, words_per_node=4), heuristics=(2,))
 
 
+@pytest.mark.parametrize("teams", [1, 2, 7, 100000])
+def test_batched_analyse_and_teams(H, teams):
+    """All layers and the AND graph in one persistent launch, split over 1, 2, 7 or one-block teams."""
+    net = synth.homln_small_overlap(2500, 7.0, 4, 0.5, 31)
+    g = H.Network(net.n, to_dev(net.layers), tuning=dict(teams=teams, words_per_node=4))
+    g.analyse(15, True)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    for i in range(4):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    check_graph(*g.and_closeness(15), ref.and_graph(15))
+    g.close()
+
+
 def test_hubs_use_block_and_warp_tiers(H):
     """A star plus a power-law layer: the centre's row exceeds the block threshold."""
     n = 5000
