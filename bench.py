@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--words", type=int, default=0, help="BFS words per node (0 = auto)")
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--teams", type=int, default=0, help="BFS teams (0 = auto)")
+    p.add_argument("--team-mix", type=int, default=0, help="1: blocks on one SM join different teams")
     p.add_argument("--single-bfs", action="store_true",
                    help="profiling aid: build the workload, run one layer's all-sources BFS once, exit")
     p.add_argument("--launch-list", action="store_true",
@@ -185,6 +186,8 @@ def run_ours(args, rank, world, dist):
         tuning["push_alpha"] = args.alpha
     if args.teams:
         tuning["teams"] = args.teams
+    if args.team_mix:
+        tuning["team_mix"] = 1
     sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
     stream = torch.cuda.current_stream(dev)
     dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]

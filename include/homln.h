@@ -115,12 +115,13 @@ typedef struct homln_accuracy_t {
 /* Tuning knobs of the multi-source BFS; zero fields take the built-in defaults. */
 typedef struct homln_tuning {
     int32_t words_per_node;  /* W: 64*W sources per BFS batch; 1, 2, 4, 8, 16 or 32 (0 = auto) */
-    int32_t push_alpha;      /* go top-down when alpha * frontier_edges < unfinished_edges (0 = default 8) */
+    int32_t push_alpha;      /* go top-down when alpha * frontier_edges < unfinished_edges (0 = default 16) */
     int32_t threads;         /* threads per block of the persistent BFS (0 = 512) */
     int32_t blocks_per_sm;   /* resident blocks per SM (0 = as many as fit) */
     int32_t relabel;         /* 1 = degree-descending relabelling of each graph before BFS, 0 = off, -1 = default */
     int32_t teams;           /* teams of blocks that run (graph, source batch) tiles concurrently (0 = auto) */
-    int32_t reserved[2];
+    int32_t team_mix;        /* 1: blocks resident on one SM join different teams; 0 (default): the same team */
+    int32_t reserved[1];
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.

@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <tuple>
 
 namespace homln {
 
@@ -48,6 +49,13 @@ void Alloc::put(void *p, size_t bytes) {
     else cudaFreeAsync(p, stream);
 }
 
+// CC nodes of one graph under one selection rule: ids in rank order and a membership bitmap.
+struct Selection {
+    DBuf<int32_t> ranked;
+    DBuf<uint32_t> bits;
+    int32_t count = 0;
+};
+
 // Partial results of one analysed graph (a layer or an AND aggregate).
 struct GraphState {
     Csr csr;
@@ -57,6 +65,7 @@ struct GraphState {
     DBuf<double> cc;
     DBuf<uint64_t> sumdist;
     DBuf<int32_t> deg;
+    std::map<std::tuple<int32_t, double, int64_t>, std::unique_ptr<Selection>> selections;
 };
 
 }  // namespace homln
@@ -260,6 +269,21 @@ GraphState &and_graph(homln_t h, uint64_t mask) {
     return ref;
 }
 
+// The graph's CC nodes under `sel`, computed once and cached (the closeness values never change).
+Selection &selection_of(homln_t h, GraphState &g, const homln_select &sel) {
+    auto key = std::make_tuple(sel.mode, sel.mode == HOMLN_TOPK_PERCENT ? sel.percent : 0.0,
+                               sel.mode == HOMLN_TOPK_COUNT ? sel.k : (int64_t)0);
+    auto it = g.selections.find(key);
+    if (it != g.selections.end()) return *it->second;
+    auto s = std::make_unique<Selection>();
+    if (!s->ranked.alloc(&h->al, h->n) || !s->bits.alloc(&h->al, ceil_div(h->n, 32)))
+        fail(HOMLN_ENOMEM, "selection");
+    s->count = select_nodes(h->n, g.cc.p, sel, s->ranked.p, s->bits.p, h->err.p, &h->al, h->stream);
+    Selection &ref = *s;
+    g.selections.emplace(key, std::move(s));
+    return ref;
+}
+
 void check_select(const homln_select *sel) {
     if (!sel) fail(HOMLN_EINVAL, "selection is NULL");
     if (sel->reserved != 0) fail(HOMLN_EINVAL, "homln_select.reserved must be 0");
@@ -362,6 +386,7 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         if (t->relabel >= 0) bt.relabel = t->relabel ? 1 : 0;
         if (t->teams < 0) fail(HOMLN_EINVAL, "teams must be >= 0");
         bt.teams = t->teams;
+        bt.team_mix = t->team_mix ? 1 : 0;
     }
     h->tuning = bt;
     API_END
@@ -435,10 +460,9 @@ homln_status homln_topk(homln_t h, int32_t which, uint64_t layer_mask, const hom
     use_device(h);
     GraphState &g = which >= 0 ? *h->layers[which] : and_graph(h, layer_mask);
     analyse(h, g);
-    DevOut<int32_t> o;
-    o.to(h, nodes_out, h->n);
-    int32_t c = select_nodes(h->n, g.cc.p, *sel, o.p, nullptr, h->err.p, &h->al, h->stream);
-    o.finish(h, c);
+    Selection &S = selection_of(h, g, *sel);
+    const int32_t c = S.count;
+    if (nodes_out && put_out(h, nodes_out, S.ranked.p, sizeof(int32_t) * c)) HCUDA(cudaStreamSynchronize(h->stream));
     check_device_error(h);
     *count_out = c;
     API_END
@@ -471,15 +495,15 @@ homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, co
         select_nodes(n, scores.p, *sel, ranked.p, bits.p, h->err.p, &h->al, h->stream);
         c = bits_to_sorted_ids(n, bits.p, o.p, &h->al, h->stream);
     } else {
-        // CC-node sets of the layers, intersected (naive), then CC1's refinement
-        DBuf<uint32_t> common, tmp;
-        DBuf<int32_t> ranked;
-        if (!common.alloc(&h->al, nw) || !tmp.alloc(&h->al, nw) || !ranked.alloc(&h->al, n))
-            fail(HOMLN_ENOMEM, "compose scratch");
+        // CC-node sets of the layers (cached per selection rule), intersected (naive), then CC1's refinement
+        DBuf<uint32_t> common;
+        if (!common.alloc(&h->al, nw)) fail(HOMLN_ENOMEM, "compose scratch");
         for (size_t k = 0; k < ids.size(); ++k) {
-            GraphState &g = *h->layers[ids[k]];
-            select_nodes(n, g.cc.p, *sel, ranked.p, k == 0 ? common.p : tmp.p, h->err.p, &h->al, h->stream);
-            if (k > 0) bits_and(nw, common.p, tmp.p, h->stream);
+            Selection &S = selection_of(h, *h->layers[ids[k]], *sel);
+            if (k == 0)
+                HCUDA(cudaMemcpyAsync(common.p, S.bits.p, sizeof(uint32_t) * nw, cudaMemcpyDeviceToDevice, h->stream));
+            else
+                bits_and(nw, common.p, S.bits.p, h->stream);
         }
         if (heuristic == HOMLN_NAIVE) {
             c = bits_to_sorted_ids(n, common.p, o.p, &h->al, h->stream);

@@ -203,7 +203,8 @@ void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, c
 struct BfsTuning {
     int W = 0;           // words per node (0 = auto)
     int teams = 0;       // teams of blocks sharing the grid (0 = auto)
-    int push_alpha = 8;
+    int team_mix = 0;    // 1: blocks sharing an SM join different teams
+    int push_alpha = 16;
     int threads = 512;
     int blocks_per_sm = 0;
     int relabel = 1;

@@ -67,31 +67,39 @@ __device__ __forceinline__ bool row_contains(const int32_t *__restrict__ col, in
     return false;
 }
 
-// One thread per vertex: walk the shortest of its rows and keep the entries found in all others.
+// One warp per vertex: the lanes walk the shortest of its rows 32 entries at a time and keep
+// the entries found (binary search) in every other row; a ballot keeps them in order.
 template <bool WRITE>
 __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, const int64_t *__restrict__ out_rp,
                            int32_t *__restrict__ out_col) {
-    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
         int best = 0;
         int64_t best_len = L.rp[0][u + 1] - L.rp[0][u];
         for (int i = 1; i < L.r; ++i) {
             int64_t len = L.rp[i][u + 1] - L.rp[i][u];
             if (len < best_len) { best_len = len; best = i; }
         }
-        int64_t b0 = L.rp[best][u];
+        const int64_t b0 = L.rp[best][u];
+        const int64_t o = WRITE ? out_rp[u] : 0;
         int32_t c = 0;
-        int64_t o = WRITE ? out_rp[u] : 0;
-        for (int64_t j = 0; j < best_len; ++j) {
-            int32_t v = L.col[best][b0 + j];
-            bool all = true;
-            for (int i = 0; i < L.r && all; ++i)
-                if (i != best) all = row_contains(L.col[i], L.rp[i][u], L.rp[i][u + 1], v);
-            if (all) {
-                if (WRITE) out_col[o + c] = v;
-                ++c;
+        for (int64_t j0 = 0; j0 < best_len; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool all = false;
+            int32_t v = 0;
+            if (j < best_len) {
+                v = L.col[best][b0 + j];
+                all = true;
+                for (int i = 0; i < L.r && all; ++i)
+                    if (i != best) all = row_contains(L.col[i], L.rp[i][u], L.rp[i][u + 1], v);
             }
+            const uint32_t m = __ballot_sync(0xffffffffu, all);
+            if (WRITE && all) out_col[o + c + __popc(m & ((1u << lane) - 1u))] = v;
+            c += __popc(m);
         }
-        if (!WRITE) cnt[u] = c;
+        if (!WRITE && lane == 0) cnt[u] = c;
     }
 }
 
@@ -212,11 +220,12 @@ void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, 
     out.n = n;
     DBuf<int32_t> cnt;
     if (!out.rowptr.alloc(al, (size_t)n + 1) || !cnt.alloc(al, n)) fail(HOMLN_ENOMEM, "and scratch");
-    launch(k_and_rows<false>, grid_for(n), 256, 0, s, n, L, cnt.p, nullptr, nullptr);
+    launch(k_and_rows<false>, grid_for((int64_t)n * 32), 256, 0, s, n, L, cnt.p, nullptr, nullptr);
     scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
     out.nnz = read_i64(out.rowptr.p + n, s);
     if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "and col");
-    if (out.nnz > 0) launch(k_and_rows<true>, grid_for(n), 256, 0, s, n, L, nullptr, out.rowptr.p, out.col.p);
+    if (out.nnz > 0)
+        launch(k_and_rows<true>, grid_for((int64_t)n * 32), 256, 0, s, n, L, nullptr, out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
 }
 

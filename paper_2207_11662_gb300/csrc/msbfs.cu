@@ -52,7 +52,12 @@ struct TeamArgs {
     uint64_t *state;            // [4 arrays][nteams][maxn * W]: seen, frontier A, frontier B, accumulator
     uint8_t *quiet;             // [nteams][maxn]
     unsigned long long *ctr;    // [nteams][16]: 3 counter slots x {new bits, frontier edges, unfinished edges}
-    uint32_t *bar;              // [nteams][32]: count, generation, ..., [8] current tile
+    uint32_t *bar;              // [nteams][32]: count, generation, ..., [8] current tile, [9] members
+    uint32_t *sm_slots;         // [number of SMs]: blocks registered on each SM so far
+    uint32_t *grid_bar;         // whole-grid barrier: count, generation
+    int32_t nsm;                // SMs of the device
+    int32_t per_sm;             // resident blocks per SM
+    int32_t team_mix;           // 1: blocks sharing an SM join different teams; 0: the same team
     int32_t *queue;             // next tile to hand out
     int32_t *err;
     int32_t atomic_fr;          // several teams may update one graph's F/R
@@ -82,6 +87,9 @@ struct Tile {
 // frontier buffers then hold zero for it and nothing can change it, so every later level
 // of the batch skips it after reading one byte.
 constexpr uint8_t QUIET = 2;
+
+// Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices.
+constexpr int kChunkPasses = 4;
 
 enum {
     ST_LEVELS, ST_PULL, ST_PUSH, ST_EDGES, ST_WORDS, ST_PUSHED, ST_BATCHES, ST_PUSHWORDS, ST_BYTES, ST_VISITS, ST_N
@@ -276,6 +284,7 @@ __device__ __forceinline__ void reset_next_slot(const Tile &a, uint32_t ps) {
         slot[0] = 0;
         slot[1] = 0;
         slot[2] = 0;
+        slot[3] = 0;  // work counter of the next pull or push phase
     }
 }
 
@@ -503,47 +512,57 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
         }
     }
-    // --- group tier: T lanes per vertex
+    // --- group tier: T lanes per vertex. Warps take chunks of vertices from the team's work
+    // counter, so a slow vertex (no early exit, long row) delays only its own chunk.
     {
-        const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
-        const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
-        for (int64_t v = a.hub_warp_end + gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-            uint8_t qv = 0;
-            if (v < a.n) {
-                qv = a.quiet[v];
-                if (STATS && q == 0) st[ST_BYTES] += 1;
-            }
-            const bool act = v < a.n && qv < QUIET;
-            uint64_t s[K], need[K], acc[K], nw[K];
-            bool lane_need = false;
-            int64_t rb = 0, re = 0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) s[k] = need[k] = acc[k] = 0;
-            if (act) {
-                ldw<K>(a.seen + v * W + q * K, s);
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    need[k] = ~s[k];
-                    lane_need |= need[k] != 0;
+        unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
+        const int64_t per_pass = 32 / T;
+        const int64_t chunk = per_pass * kChunkPasses;
+        const int64_t nrest = a.n - a.hub_warp_end;
+        for (;;) {
+            long long base = 0;
+            if (lane == 0) base = (long long)atomicAdd(work, (unsigned long long)chunk);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= nrest) break;  // uniform over the warp
+            const int64_t vend = a.hub_warp_end + min((int64_t)base + chunk, nrest);
+            for (int64_t v = a.hub_warp_end + base + lane / T; __any_sync(0xffffffffu, v < vend); v += per_pass) {
+                uint8_t qv = 0;
+                if (v < vend) {
+                    qv = a.quiet[v];
+                    if (STATS && q == 0) st[ST_BYTES] += 1;
                 }
-                rb = a.rowptr[v];
-                re = a.rowptr[v + 1];
-            }
-            // every lane must take part in the shuffle, so no short-circuit around it
-            const bool group_needs = group_any<T>(lane_need);
-            const bool full0 = act && !group_needs;
-            int64_t it = 0;
-            if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
-            if (STATS) {
-                st[ST_WORDS] += it * K;
-                st[ST_BYTES] += it * 8 * K;
-                int64_t gm = group_max<T>(it);
-                if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
-                if (act) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
-            }
+                const bool act = v < vend && qv < QUIET;
+                uint64_t s[K], need[K], acc[K], nw[K];
+                bool lane_need = false;
+                int64_t rb = 0, re = 0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-            commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
+                for (int k = 0; k < K; ++k) s[k] = need[k] = acc[k] = 0;
+                if (act) {
+                    ldw<K>(a.seen + v * W + q * K, s);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        need[k] = ~s[k];
+                        lane_need |= need[k] != 0;
+                    }
+                    rb = a.rowptr[v];
+                    re = a.rowptr[v + 1];
+                }
+                // every lane must take part in the shuffle, so no short-circuit around it
+                const bool group_needs = group_any<T>(lane_need);
+                const bool full0 = act && !group_needs;
+                int64_t it = 0;
+                if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
+                if (STATS) {
+                    st[ST_WORDS] += it * K;
+                    st[ST_BYTES] += it * 8 * K;
+                    int64_t gm = group_max<T>(it);
+                    if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
+                    if (act) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
+                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
+            }
         }
     }
     flush_counters(a, c, ps);
@@ -552,7 +571,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
 // Top-down level: frontier vertices OR their words into the neighbours' accumulators
 // (quiet neighbours are full and are skipped).
 template <int W, bool STATS>
-__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, unsigned long long *st) {
+__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint32_t ps, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
@@ -582,9 +601,19 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, unsi
     const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
     for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) push_row(v, lane / T, 32 / T);
-    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
-    const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
-    for (int64_t v = a.hub_warp_end + gtid / T; v < a.n; v += G) push_row(v, 0, 1);
+    // group tier: chunks from the team's work counter (this phase's slot, cleared beforehand)
+    unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
+    const int64_t per_pass = 32 / T;
+    const int64_t chunk = per_pass * kChunkPasses;
+    const int64_t nrest = a.n - a.hub_warp_end;
+    for (;;) {
+        long long base = 0;
+        if (lane == 0) base = (long long)atomicAdd(work, (unsigned long long)chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= nrest) break;
+        const int64_t vend = a.hub_warp_end + min((int64_t)base + chunk, nrest);
+        for (int64_t v = a.hub_warp_end + base + lane / T; v < vend; v += per_pass) push_row(v, 0, 1);
+    }
 }
 
 // The levels of one batch (sources s0 .. s0+ns-1) of one graph, run by one team.
@@ -605,7 +634,7 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
         if (newbits == 0) break;
         const bool push = (unsigned long long)a.push_alpha * mf < mu;
         if (push) {
-            phase_push<W, STATS>(a, cur, st);
+            phase_push<W, STATS>(a, cur, ps, st);
             if (!team_sync(tb)) return false;
             phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
         } else {
@@ -619,16 +648,38 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
     return true;
 }
 
+__device__ __forceinline__ uint32_t sm_id() {
+    uint32_t id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
 template <int W, bool STATS>
 __global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
     PhaseCounters c;
     unsigned long long st[ST_N];
 #pragma unroll
     for (int i = 0; i < ST_N; ++i) st[i] = 0;
-    const int team = (int)(blockIdx.x % (unsigned)A.nteams);
-    const int rank = (int)(blockIdx.x / (unsigned)A.nteams);
-    const int tsize = (int)(gridDim.x / (unsigned)A.nteams);
+    // Join a team by SM. By default the blocks that share an SM join the same team (they
+    // then share its L1 for the team's frontier gathers: faster on the 50,000-node
+    // power-law workload); with team_mix they join different teams instead.
+    __shared__ int s_team, s_rank;
+    if (threadIdx.x == 0) {
+        const uint32_t sm = sm_id() % (uint32_t)A.nsm;
+        const uint32_t slot = atomicAdd(A.sm_slots + sm, 1u);
+        const uint32_t spread = !A.team_mix ? 0u : A.nteams >= A.per_sm ? (uint32_t)(A.nteams / A.per_sm) : 1u;
+        const int tm = (int)((sm + slot * spread) % (uint32_t)A.nteams);
+        s_team = tm;
+        s_rank = (int)atomicAdd(A.bar + (size_t)tm * 32 + 9, 1u);
+    }
+    {
+        const TeamBarrier all{A.grid_bar, A.grid_bar + 1, A.err, gridDim.x};
+        if (!team_sync(all)) return;
+    }
+    const int team = s_team;
+    const int rank = s_rank;
     uint32_t *tbar = A.bar + (size_t)team * 32;
+    const int tsize = (int)*(volatile uint32_t *)(tbar + 9);
     const TeamBarrier tb{tbar, tbar + 1, A.err, (uint32_t)tsize};
     const size_t stride = (size_t)A.maxn * W;
     const size_t arr = stride * A.nteams;
@@ -780,9 +831,8 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
-    int grid = nsm * per_sm;
+    const int grid = nsm * per_sm;
     if (nteams > grid) nteams = grid;
-    grid -= grid % nteams;
 
     // relabel each graph by degree and find its hub tiers
     const size_t ng = jobs.size();
@@ -836,13 +886,14 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     DBuf<uint32_t> barmem;
     DBuf<int32_t> queue;
     DBuf<GraphDesc> d_desc;
+    const size_t bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
     if (!state.alloc(al, 4 * words) || !quiet.alloc(al, (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
-        !barmem.alloc(al, 32 * nteams) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
+        !barmem.alloc(al, bar_words) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
         fail(HOMLN_ENOMEM, "bfs state");
     if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
     HCUDA(cudaMemsetAsync(state.p + 3 * words, 0, words * sizeof(uint64_t), s));  // accumulators
     HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
-    HCUDA(cudaMemsetAsync(barmem.p, 0, 32 * nteams * sizeof(uint32_t), s));
+    HCUDA(cudaMemsetAsync(barmem.p, 0, bar_words * sizeof(uint32_t), s));
     HCUDA(cudaMemsetAsync(queue.p, 0, sizeof(int32_t), s));
     HCUDA(cudaMemcpyAsync(d_desc.p, desc.data(), ng * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
     if (stats) HCUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
@@ -852,12 +903,17 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     A.ngraphs = (int32_t)ng;
     A.ntiles = tile;
     A.nteams = nteams;
-    A.push_alpha = t.push_alpha > 0 ? t.push_alpha : 8;
+    A.push_alpha = t.push_alpha > 0 ? t.push_alpha : 16;
     A.maxn = maxn;
     A.state = state.p;
     A.quiet = quiet.p;
     A.ctr = ctr.p;
     A.bar = barmem.p;
+    A.grid_bar = barmem.p + 32 * (size_t)nteams;
+    A.sm_slots = barmem.p + 32 * (size_t)nteams + 32;
+    A.nsm = nsm;
+    A.per_sm = per_sm;
+    A.team_mix = t.team_mix;
     A.queue = queue.p;
     A.err = d_err;
     A.atomic_fr = nteams > 1 ? 1 : 0;

@@ -85,10 +85,36 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const T *__restrict__ in, 
     }
 }
 
+// A scan that fits one tile: one block, one launch; writes the total to out[n].
+template <typename T>
+__global__ void __launch_bounds__(SCAN_T) k_scan_single(const T *__restrict__ in, int64_t *out, int64_t n) {
+    int64_t base = (int64_t)threadIdx.x * SCAN_I;
+    int64_t vals[SCAN_I];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        vals[i] = (base + i < n) ? (int64_t)in[base + i] : 0;
+        s += vals[i];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan<T>(s, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += vals[i];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 template <typename T>
 void scan_impl(const T *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) {
     if (n <= 0) {
         HCUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return;
+    }
+    if (n <= SCAN_TILE) {
+        launch(k_scan_single<T>, 1, SCAN_T, 0, s, in, out, n);
+        HCUDA(cudaGetLastError());
         return;
     }
     int64_t nb = ceil_div(n, SCAN_TILE);

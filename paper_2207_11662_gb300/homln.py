@@ -51,7 +51,8 @@ class homln_accuracy_t(ctypes.Structure):
 
 class homln_tuning(ctypes.Structure):
     _fields_ = [("words_per_node", c_int32), ("push_alpha", c_int32), ("threads", c_int32),
-                ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("reserved", c_int32 * 2)]
+                ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("team_mix", c_int32),
+                ("reserved", c_int32 * 1)]
 
 
 class homln_profile_t(ctypes.Structure):
@@ -186,8 +187,9 @@ def homln_destroy(h) -> None:
     _check(lib.homln_destroy(h), "homln_destroy")
 
 
-def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0) -> None:
-    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams)
+def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0,
+                     team_mix=0) -> None:
+    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix)
     _check(lib.homln_set_tuning(h, ctypes.byref(t)), "homln_set_tuning")
 
 

@@ -116,11 +116,11 @@ def test_push_pull_extremes(H, alpha):
     full_parity(H, net, sel, tuning=dict(push_alpha=alpha, words_per_node=4), heuristics=(2,))
 
 
-@pytest.mark.parametrize("teams", [1, 2, 7, 100000])
-def test_batched_analyse_and_teams(H, teams):
+@pytest.mark.parametrize("teams,mix", [(1, 0), (2, 1), (7, 0), (7, 1), (100000, 0)])
+def test_batched_analyse_and_teams(H, teams, mix):
     """All layers and the AND graph in one persistent launch, split over 1, 2, 7 or one-block teams."""
     net = synth.homln_small_overlap(2500, 7.0, 4, 0.5, 31)
-    g = H.Network(net.n, to_dev(net.layers), tuning=dict(teams=teams, words_per_node=4))
+    g = H.Network(net.n, to_dev(net.layers), tuning=dict(teams=teams, words_per_node=4, team_mix=mix))
     g.analyse(15, True)
     ref = O.OracleHoMLN(net.n, net.layers, threads=8)
     for i in range(4):
