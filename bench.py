@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--teams", type=int, default=0, help="BFS teams (0 = auto)")
     p.add_argument("--team-mix", type=int, default=0, help="1: blocks on one SM join different teams")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
+    p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--single-bfs", action="store_true",
                    help="profiling aid: build the workload, run one layer's all-sources BFS once, exit")
     p.add_argument("--launch-list", action="store_true",
@@ -332,6 +334,77 @@ def run_ours(args, rank, world, dist):
     return result, net
 
 
+def batch_vs_plain(args, dev):
+    """64 HoMLNs (2-8 layers, 500-20,000 nodes, ER or BA layers): all their layers and AND graphs
+    analysed (a) in one persistent launch over every (graph, batch) tile, autotuned, (b) one
+    persistent launch per HoMLN, (c) plain -- one ordinary launch per BFS phase with the host driving
+    the levels, layer by layer. Outputs must be bit-identical across the three."""
+    import torch
+    from paper_2207_11662_gb300 import autotune
+    from paper_2207_11662_gb300 import homln as H
+    from paper_2207_11662_gb300 import synth
+
+    nets = synth.homln_batch(args.batch_count, 3001)
+    stream = torch.cuda.current_stream(dev)
+    hs = [H.homln_create(net.n, [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers],
+                         stream=stream.cuda_stream) for net in nets]
+    masks = [(1 << net.n_layers) - 1 for net in nets]
+    work = 0
+    edges = []
+    for net in nets:
+        w, ec = teps_work(net.n, net.layers)
+        work += w
+        edges += ec
+    ns = [net.n for net in nets]
+    outs = [[torch.empty(net.n, dtype=torch.int64, device=dev) for _ in range(net.n_layers + 1)] for net in nets]
+
+    def collect():
+        snap = []
+        for h, net, mask, o in zip(hs, nets, masks, outs):
+            for i in range(net.n_layers):
+                H.homln_layer_closeness(h, i, o[i], None, None)
+            H.homln_and_closeness(h, mask, o[-1], None, None)
+            snap.append([t.clone() for t in o])
+        return snap
+
+    def timed(fn, reps=3):
+        best = []
+        for _ in range(reps):
+            for h in hs:
+                H.homln_invalidate(h)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            best.append(e0.elapsed_time(e1))
+        return statistics.mean(best)
+
+    tuning, tune_log = autotune.tune(hs, masks, ns, edges, True, stream.cuda_stream, use_cache=False)
+    H.homln_set_tuning(hs[0], **tuning)
+    timed(lambda: H.homln_batch_analyse(hs, masks, True), reps=1)  # warm-up
+    t_batch = timed(lambda: H.homln_batch_analyse(hs, masks, True))
+    ref = collect()
+    for h in hs:
+        H.homln_set_tuning(h)
+    t_per = timed(lambda: [H.homln_analyse(h, m, True) for h, m in zip(hs, masks)])
+    same = all(torch.equal(a, b) for x, y in zip(ref, collect()) for a, b in zip(x, y))
+    for h in hs:
+        H.homln_set_tuning(h, schedule=1)
+    t_plain = timed(lambda: [H.homln_analyse(h, m, True) for h, m in zip(hs, masks)], reps=1)
+    same = same and all(torch.equal(a, b) for x, y in zip(ref, collect()) for a, b in zip(x, y))
+    for h in hs:
+        H.homln_destroy(h)
+    return {"workload": f"{len(nets)} HoMLNs, {sum(n.n_layers for n in nets)} layers + {len(nets)} AND graphs, "
+                        f"n in [{min(ns)}, {max(ns)}], ER/BA layers",
+            "batched_ms": round(t_batch, 3), "per_homln_persistent_ms": round(t_per, 3),
+            "plain_ms": round(t_plain, 3), "speedup_vs_plain": round(t_plain / t_batch, 2),
+            "speedup_vs_per_homln": round(t_per / t_batch, 2), "batched_gteps": round(work / t_batch / 1e6, 1),
+            "identical_outputs": bool(same), "autotuned": tuning,
+            "autotune_candidates_ms": tune_log["candidates"]}
+
+
 def cpu_baseline(net, sources_per_graph: int, seed: int = 2001):
     """The oracle as it stands: queue BFS from a seeded sample of sources on every analysed graph."""
     from oracle import oracle as O
@@ -388,6 +461,9 @@ def main():
     if result is None:
         return
     if rank == 0:
+        if not args.no_batch:
+            import torch
+            result["batched_vs_plain"] = batch_vs_plain(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)
         print(json.dumps(result))

@@ -121,7 +121,9 @@ typedef struct homln_tuning {
     int32_t relabel;         /* 1 = degree-descending relabelling of each graph before BFS, 0 = off, -1 = default */
     int32_t teams;           /* teams of blocks that run (graph, source batch) tiles concurrently (0 = auto) */
     int32_t team_mix;        /* 1: blocks resident on one SM join different teams; 0 (default): the same team */
-    int32_t reserved[1];
+    int32_t schedule;        /* 0 (default): one persistent launch over all (graph, batch) tiles;
+                                1: plain -- one ordinary launch per BFS phase, levels driven by the host
+                                   (the comparison baseline; identical results) */
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.
@@ -163,6 +165,15 @@ HOMLN_API homln_status homln_layer_closeness(homln_t h, int32_t layer, uint64_t 
  * calls then only copy them out. Asynchronous on the handle's stream.
  * Errors: EINVAL (mask), ENOMEM, ECUDA; device errors surface at the next synchronising call. */
 HOMLN_API homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t with_and);
+
+/* Psi for many HoMLNs in one persistent launch: for every handle nets[i], the layers in
+ * masks[i] and (with_and != 0) their AND aggregate. The BFS tiles of all these graphs share
+ * one device work queue, so small and large graphs balance across the GPU. All handles must
+ * live on one device; the launch runs on nets[0]'s stream with nets[0]'s tuning, allocator
+ * and error word, and the other handles' streams are ordered before and after it with events.
+ * Results are cached in each handle exactly as homln_analyse would cache them.
+ * Errors: EINVAL (null handle, masks, devices), ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_batch_analyse(homln_t *nets, int32_t count, const uint64_t *masks, int32_t with_and);
 
 /* Boolean AND aggregation of the layers in `layer_mask` (Section 3.1, Section 4 ground truth):
  * an edge is kept iff it is present in every selected layer. The AND graph is built
@@ -251,6 +262,10 @@ HOMLN_API homln_status homln_get_profile(homln_t h, homln_profile_t *out);
 HOMLN_API homln_status homln_reset_profile(homln_t h);
 /* Number of kernels this library has launched in the process so far. */
 HOMLN_API int64_t homln_kernel_launches(void);
+
+/* Drop the cached Psi results (closeness, farness, selections) of every graph of the handle;
+ * the CSRs and AND graphs stay. The next query recomputes them (used to re-measure). */
+HOMLN_API homln_status homln_invalidate(homln_t h);
 
 /* Wait for all work queued by the handle and report any device-side error it raised. */
 HOMLN_API homln_status homln_sync(homln_t h);

@@ -66,6 +66,8 @@ struct GraphState {
     DBuf<uint64_t> sumdist;
     DBuf<int32_t> deg;
     std::map<std::tuple<int32_t, double, int64_t>, std::unique_ptr<Selection>> selections;
+    BfsGraph bfs;          // the graph as the BFS reads it (built once, kept by homln_invalidate)
+    bool bfs_ready = false;
 };
 
 }  // namespace homln
@@ -189,19 +191,39 @@ struct DevOut {
     }
 };
 
-// Psi for every graph in `gs` that is not analysed yet, in one persistent BFS launch.
-void analyse_many(homln_t h, const std::vector<GraphState *> &gs) {
-    std::vector<GraphState *> todo;
-    for (GraphState *g : gs)
-        if (!g->analysed && std::find(todo.begin(), todo.end(), g) == todo.end()) todo.push_back(g);
+// Psi for every (handle, graph) item not analysed yet, in one persistent BFS launch on the
+// stream of `h` (the other handles' streams are ordered around it with events). Each graph's
+// outputs are allocated through its own handle.
+void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>> &items) {
+    std::vector<std::pair<homln_t, GraphState *>> todo;
+    for (const auto &it : items)
+        if (!it.second->analysed &&
+            std::find_if(todo.begin(), todo.end(), [&](const auto &x) { return x.second == it.second; }) == todo.end())
+            todo.push_back(it);
     if (todo.empty()) return;
-    const int32_t n = h->n;
     std::vector<BfsJob> jobs;
-    for (GraphState *g : todo) {
-        if (!g->F.alloc(&h->al, n) || !g->R.alloc(&h->al, n) || !g->cc.alloc(&h->al, n) ||
-            !g->sumdist.alloc(&h->al, n) || !g->deg.alloc(&h->al, n))
+    std::vector<homln_t> others;
+    for (const auto &it : todo) {
+        homln_t o = it.first;
+        GraphState *g = it.second;
+        const int32_t n = o->n;
+        if (!g->F.alloc(&o->al, n) || !g->R.alloc(&o->al, n) || !g->cc.alloc(&o->al, n) ||
+            !g->sumdist.alloc(&o->al, n) || !g->deg.alloc(&o->al, n))
             fail(HOMLN_ENOMEM, "closeness outputs");
-        jobs.push_back(BfsJob{&g->csr, g->F.p, g->R.p});
+        if (!g->bfs_ready || g->bfs.relabeled != (h->tuning.relabel != 0)) {
+            bfs_prepare(g->csr, h->tuning.relabel != 0, g->bfs, &o->al, o->stream);
+            g->bfs_ready = true;
+        }
+        jobs.push_back(BfsJob{&g->bfs, g->F.p, g->R.p});
+        if (o != h && o->stream != h->stream && std::find(others.begin(), others.end(), o) == others.end())
+            others.push_back(o);
+    }
+    for (homln_t o : others) {  // h's stream waits for the CSRs and outputs queued on the other streams
+        cudaEvent_t e;
+        HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        HCUDA(cudaEventRecord(e, o->stream));
+        HCUDA(cudaStreamWaitEvent(h->stream, e, 0));
+        cudaEventDestroy(e);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling) {
@@ -226,10 +248,24 @@ void analyse_many(homln_t h, const std::vector<GraphState *> &gs) {
         h->stats.teams = st.teams;
     }
     h->bfs_launches += 1;
-    for (GraphState *g : todo) {
-        closeness_finalize(n, g->csr.rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p, g->deg.p, h->stream);
+    for (const auto &it : todo) {
+        GraphState *g = it.second;
+        closeness_finalize(it.first->n, g->csr.rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p, g->deg.p, h->stream);
         g->analysed = true;
     }
+    for (homln_t o : others) {  // and the other streams wait for the results
+        cudaEvent_t e;
+        HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        HCUDA(cudaEventRecord(e, h->stream));
+        HCUDA(cudaStreamWaitEvent(o->stream, e, 0));
+        cudaEventDestroy(e);
+    }
+}
+
+void analyse_many(homln_t h, const std::vector<GraphState *> &gs) {
+    std::vector<std::pair<homln_t, GraphState *>> items;
+    for (GraphState *g : gs) items.push_back({h, g});
+    analyse_items(h, items);
 }
 
 void analyse(homln_t h, GraphState &g) { analyse_many(h, {&g}); }
@@ -387,6 +423,8 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         if (t->teams < 0) fail(HOMLN_EINVAL, "teams must be >= 0");
         bt.teams = t->teams;
         bt.team_mix = t->team_mix ? 1 : 0;
+        if (t->schedule < 0 || t->schedule > 1) fail(HOMLN_EINVAL, "schedule must be 0 or 1");
+        bt.schedule = t->schedule;
     }
     h->tuning = bt;
     API_END
@@ -411,6 +449,24 @@ homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t with_and) {
     for (int i : mask_layers(h, layer_mask)) gs.push_back(h->layers[i].get());
     if (with_and) gs.push_back(&and_graph(h, layer_mask));
     analyse_many(h, gs);
+    API_END
+}
+
+homln_status homln_batch_analyse(homln_t *nets, int32_t count, const uint64_t *masks, int32_t with_and) {
+    API_BEGIN
+    if (!nets || !masks || count < 1) fail(HOMLN_EINVAL, "nets, masks and count >= 1 are required");
+    for (int32_t i = 0; i < count; ++i)
+        if (!nets[i]) fail(HOMLN_EINVAL, "null handle in nets");
+    homln_t h = nets[0];
+    for (int32_t i = 1; i < count; ++i)
+        if (nets[i]->device != h->device) fail(HOMLN_EINVAL, "all handles must live on one device");
+    use_device(h);
+    std::vector<std::pair<homln_t, GraphState *>> items;
+    for (int32_t i = 0; i < count; ++i) {
+        for (int l : mask_layers(nets[i], masks[i])) items.push_back({nets[i], nets[i]->layers[l].get()});
+        if (with_and) items.push_back({nets[i], &and_graph(nets[i], masks[i])});
+    }
+    analyse_items(h, items);
     API_END
 }
 
@@ -540,6 +596,24 @@ homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, cons
     accuracy_counts(h->n, p.p, n_pred, t.p, n_truth, &r, h->err.p, &h->al, h->stream);
     check_device_error(h);
     *out = r;
+    API_END
+}
+
+homln_status homln_invalidate(homln_t h) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    use_device(h);
+    auto drop = [](GraphState &g) {
+        g.analysed = false;
+        g.selections.clear();
+        g.F.release();
+        g.R.release();
+        g.cc.release();
+        g.sumdist.release();
+        g.deg.release();
+    };
+    for (auto &g : h->layers) drop(*g);
+    for (auto &kv : h->ands) drop(*kv.second);
     API_END
 }
 

@@ -204,6 +204,7 @@ struct BfsTuning {
     int W = 0;           // words per node (0 = auto)
     int teams = 0;       // teams of blocks sharing the grid (0 = auto)
     int team_mix = 0;    // 1: blocks sharing an SM join different teams
+    int schedule = 0;    // 0: persistent tile queue; 1: plain, one launch per phase, host-driven levels
     int push_alpha = 16;
     int threads = 512;
     int blocks_per_sm = 0;
@@ -223,9 +224,17 @@ struct BfsStats {  // filled by an instrumented run
     int teams = 0;             // teams of the last launch
 };
 
+// The graph the BFS traverses: the CSR itself, or its degree-descending relabelling (perm[new] = old).
+struct BfsGraph {
+    Csr csr;
+    DBuf<int32_t> perm;
+    bool relabeled = false;
+};
+void bfs_prepare(const Csr &g, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s);
+
 struct BfsJob {
-    const Csr *g;
-    uint64_t *F;
+    const BfsGraph *g;
+    uint64_t *F;  // outputs in the original vertex order
     uint32_t *R;
 };
 
@@ -233,11 +242,6 @@ struct BfsJob {
 void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
                  BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop);
 
-// All-sources BFS: F[v] = sum of distances, R[v] = reachable count (v excluded).
-// ev_start/ev_stop (optional) are recorded on `s` right around the BFS kernel launch.
-void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuning &t, int32_t *d_err,
-                       Alloc *al, cudaStream_t s, BfsStats *stats, float *kernel_ms, cudaEvent_t ev_start = nullptr,
-                       cudaEvent_t ev_stop = nullptr);
 int msbfs_pick_words(int32_t n, int64_t nnz);
 
 // ---------------------------------------------------------------------------

@@ -248,7 +248,9 @@ void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, c
     if (!vkeys.alloc(al, n) || !inv.alloc(al, n) || !newdeg.alloc(al, n) || !perm.alloc(al, n))
         fail(HOMLN_ENOMEM, "relabel scratch");
     launch(k_degree_keys, grid_for(n), 256, 0, s, n, g.rowptr.p, vkeys.p);
-    radix_sort_u64(vkeys.p, nullptr, n, 0, 2 * NODE_BITS, al, s);
+    // the keys are generated in id order, so a stable sort on the degree bits alone leaves equal
+    // degrees in ascending id order
+    radix_sort_u64(vkeys.p, nullptr, n, NODE_BITS, 2 * NODE_BITS, al, s);
     launch(k_perm_from_keys, grid_for(n), 256, 0, s, n, vkeys.p, g.rowptr.p, perm.p, inv.p, newdeg.p);
     out.n = n;
     out.nnz = g.nnz;

@@ -37,8 +37,7 @@ struct GraphDesc {
     int32_t n;
     int32_t nbatches;
     int32_t tile0;          // index of this graph's first tile
-    int32_t hub_block_end;  // vertices [0, hub_block_end) are handled by a whole block
-    int32_t hub_warp_end;   // vertices [hub_block_end, hub_warp_end) by a whole warp
+    int32_t by_degree;      // rows are in descending degree order (the hub tiers apply)
     int32_t pad;
 };
 
@@ -63,6 +62,16 @@ struct TeamArgs {
     int32_t atomic_fr;          // several teams may update one graph's F/R
     unsigned long long *stats;
 };
+
+// First vertex of a degree-descending graph whose degree is below thr (binary search).
+__device__ __forceinline__ int32_t first_below(const int64_t *__restrict__ rp, int32_t n, int64_t thr) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (rp[mid + 1] - rp[mid] >= thr) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 // One tile as seen by one block: the graph, the team's state, the block's place in the team.
 struct Tile {
@@ -713,8 +722,9 @@ __global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
         a.R = g.R;
         a.ctr = ctr;
         a.n = g.n;
-        a.hub_block_end = g.hub_block_end;
-        a.hub_warp_end = g.hub_warp_end;
+        // hub tiers: rows of at least 4 iterations per slot go to a whole block / a whole warp
+        a.hub_block_end = g.by_degree ? first_below(g.rowptr, g.n, 4 * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+        a.hub_warp_end = g.by_degree ? max(a.hub_block_end, first_below(g.rowptr, g.n, 4 * (32 / Geo<W>::T))) : 0;
         a.rank = rank;
         a.tsize = tsize;
         a.push_alpha = A.push_alpha;
@@ -740,23 +750,82 @@ __global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
     }
 }
 
+// One phase of one graph as an ordinary (non-cooperative) launch: the plain schedule, in
+// which the host drives the levels and kernel boundaries replace the team barrier.
+enum PhaseKind { PH_START = 0, PH_FINALIZE = 1, PH_PULL = 2, PH_PUSH = 3 };
+
+template <int W, bool STATS>
+__global__ void __launch_bounds__(512, 2) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
+                                                  int32_t level, uint32_t ps, int32_t cur_is_a) {
+    PhaseCounters c;
+    unsigned long long st[ST_N];
+#pragma unroll
+    for (int i = 0; i < ST_N; ++i) st[i] = 0;
+    const GraphDesc &g = A.graphs[gi];
+    const size_t arr = (size_t)A.maxn * W;
+    uint64_t *fa = A.state + 1 * arr, *fb = A.state + 2 * arr;
+    Tile a;
+    a.rowptr = g.rowptr;
+    a.col = g.col;
+    a.seen = A.state;
+    a.acc = A.state + 3 * arr;
+    a.quiet = A.quiet;
+    a.F = g.F;
+    a.R = g.R;
+    a.ctr = A.ctr;
+    a.n = g.n;
+    a.hub_block_end = g.by_degree ? first_below(g.rowptr, g.n, 4 * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+    a.hub_warp_end = g.by_degree ? max(a.hub_block_end, first_below(g.rowptr, g.n, 4 * (32 / Geo<W>::T))) : 0;
+    a.rank = blockIdx.x;
+    a.tsize = gridDim.x;
+    a.push_alpha = A.push_alpha;
+    a.atomic_fr = false;
+    uint64_t *cur = cur_is_a ? fa : fb, *nxt = cur_is_a ? fb : fa;
+    switch (kind) {
+    case PH_START: phase_start_batch<W, STATS>(a, s0, ns, st); break;
+    case PH_FINALIZE: phase_finalize<W, STATS>(a, nxt, level, ps, c, st); break;
+    case PH_PULL: phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st); break;
+    default: phase_push<W, STATS>(a, cur, ps, st); break;
+    }
+    if (STATS && A.stats) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) {
+            if (kind == PH_START) { atomicAdd(A.stats + ST_BATCHES, 1ull); }
+            if (kind == PH_PULL) { atomicAdd(A.stats + ST_LEVELS, 1ull); atomicAdd(A.stats + ST_PULL, 1ull); }
+            if (kind == PH_FINALIZE) { atomicAdd(A.stats + ST_LEVELS, 1ull); atomicAdd(A.stats + ST_PUSH, 1ull); }
+        }
+        atomicAdd(A.stats + ST_EDGES, st[ST_EDGES]);
+        atomicAdd(A.stats + ST_WORDS, st[ST_WORDS]);
+        atomicAdd(A.stats + ST_PUSHED, st[ST_PUSHED]);
+        atomicAdd(A.stats + ST_PUSHWORDS, st[ST_PUSHWORDS]);
+        atomicAdd(A.stats + ST_BYTES, st[ST_BYTES]);
+        atomicAdd(A.stats + ST_VISITS, st[ST_VISITS]);
+    }
+}
+
+typedef void (*PhaseKernel)(TeamArgs, int32_t, int32_t, int32_t, int32_t, int32_t, uint32_t, int32_t);
+
+template <int W>
+PhaseKernel pick_phase(bool stats) {
+    return stats ? k_phase<W, true> : k_phase<W, false>;
+}
+
+PhaseKernel phase_kernel_for(int W, bool stats) {
+    switch (W) {
+    case 1: return pick_phase<1>(stats);
+    case 2: return pick_phase<2>(stats);
+    case 4: return pick_phase<4>(stats);
+    case 8: return pick_phase<8>(stats);
+    case 16: return pick_phase<16>(stats);
+    case 32: return pick_phase<32>(stats);
+    default: fail(HOMLN_EINVAL, "words_per_node must be 1, 2, 4, 8, 16 or 32");
+    }
+}
+
 __global__ void k_scatter_back(int32_t n, const int32_t *__restrict__ perm, const uint64_t *__restrict__ Fi,
                                const uint32_t *__restrict__ Ri, uint64_t *__restrict__ F, uint32_t *__restrict__ R) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         F[perm[i]] = Fi[i];
         R[perm[i]] = Ri[i];
-    }
-}
-
-// Since the relabelled rows are sorted by degree (descending), the tier boundaries are
-// the first rows whose degree falls below each threshold.
-__global__ void k_tier_bounds(int32_t n, const int64_t *__restrict__ rp, int64_t block_deg, int64_t warp_deg,
-                              int32_t *out) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int64_t d = rp[i + 1] - rp[i];
-        int64_t dn = i + 1 < n ? rp[i + 2] - rp[i + 1] : -1;
-        if (d >= block_deg && dn < block_deg) out[0] = i + 1;
-        if (d >= warp_deg && dn < warp_deg) out[1] = i + 1;
     }
 }
 
@@ -801,23 +870,24 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     int32_t maxn = 0;
     int64_t maxnnz = 0;
     for (const BfsJob &j : jobs) {
-        maxn = std::max(maxn, j.g->n);
-        maxnnz = std::max(maxnnz, j.g->nnz);
+        maxn = std::max(maxn, j.g->csr.n);
+        maxnnz = std::max(maxnnz, j.g->csr.nnz);
     }
     if (maxn <= 0) return;
     const int threads = t.threads > 0 ? t.threads : 512;
     if (threads % 32 != 0 || threads > 512 || threads < 64) fail(HOMLN_EINVAL, "threads must be 64..512, multiple of 32");
 
+    const bool plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
-    int nteams = t.teams > 0 ? t.teams : kDefaultTeams;
+    int nteams = plain ? 1 : (t.teams > 0 ? t.teams : kDefaultTeams);
     int W = t.W;
     if (W <= 0) {
         W = msbfs_pick_words(maxn, maxnnz);
         while (W > 1 && nteams * 4.0 * maxn * 8.0 * W > kStateBudget) W >>= 1;
     }
-    if (t.teams <= 0) {  // no more teams than tiles
+    if (t.teams <= 0 && !plain) {  // no more teams than tiles
         int64_t tiles = 0;
-        for (const BfsJob &j : jobs) tiles += ceil_div(j.g->n, 64 * W);
+        for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
         if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
     }
     const int T = W >= 2 ? W / 2 : 1;
@@ -828,55 +898,39 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     HCUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     HCUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) fail(HOMLN_ECUDA, "device does not support cooperative launch");
+    PhaseKernel pkern = plain ? phase_kernel_for(W, stats != nullptr) : nullptr;
     HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
     const int grid = nsm * per_sm;
     if (nteams > grid) nteams = grid;
 
-    // relabel each graph by degree and find its hub tiers
+    // graph descriptors; relabelled graphs accumulate into scratch and are scattered back after
     const size_t ng = jobs.size();
-    std::vector<Csr> rl(ng);
-    std::vector<DBuf<int32_t>> perm(ng);
     std::vector<DBuf<uint64_t>> Fi(ng);
     std::vector<DBuf<uint32_t>> Ri(ng);
     std::vector<GraphDesc> desc(ng);
-    DBuf<int32_t> tiers;
-    if (!tiers.alloc(al, 2 * ng)) fail(HOMLN_ENOMEM, "bfs tiers");
-    HCUDA(cudaMemsetAsync(tiers.p, 0, 2 * ng * sizeof(int32_t), s));
-    const int64_t slots_block = threads / T, slots_warp = 32 / T;
     int32_t tile = 0;
     for (size_t i = 0; i < ng; ++i) {
-        const Csr *G = jobs[i].g;
+        const BfsGraph &G = *jobs[i].g;
         GraphDesc &d = desc[i];
-        d.n = G->n;
-        d.nbatches = (int32_t)ceil_div(G->n, 64 * W);
+        d.n = G.csr.n;
+        d.nbatches = (int32_t)ceil_div(d.n, 64 * W);
         d.tile0 = tile;
         tile += d.nbatches;
-        if (t.relabel) {
-            relabel_by_degree(*G, rl[i], perm[i], al, s);
-            if (!Fi[i].alloc(al, G->n) || !Ri[i].alloc(al, G->n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
-            G = &rl[i];
+        d.by_degree = G.relabeled ? 1 : 0;
+        d.rowptr = G.csr.rowptr.p;
+        d.col = G.csr.col.p;
+        if (G.relabeled) {
+            if (!Fi[i].alloc(al, d.n) || !Ri[i].alloc(al, d.n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
             d.F = Fi[i].p;
             d.R = Ri[i].p;
-            if (G->nnz > 0)
-                launch(k_tier_bounds, (unsigned)ceil_div(G->n, 256), 256, 0, s, G->n, G->rowptr.p, 4 * slots_block,
-                       4 * slots_warp, tiers.p + 2 * i);
         } else {
             d.F = jobs[i].F;
             d.R = jobs[i].R;
         }
-        d.rowptr = G->rowptr.p;
-        d.col = G->col.p;
-        HCUDA(cudaMemsetAsync(d.F, 0, (size_t)G->n * sizeof(uint64_t), s));
-        HCUDA(cudaMemsetAsync(d.R, 0, (size_t)G->n * sizeof(uint32_t), s));
-    }
-    std::vector<int32_t> h_tiers(2 * ng, 0);
-    HCUDA(cudaMemcpyAsync(h_tiers.data(), tiers.p, 2 * ng * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    HCUDA(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < ng; ++i) {
-        desc[i].hub_block_end = h_tiers[2 * i];
-        desc[i].hub_warp_end = std::max(h_tiers[2 * i + 1], h_tiers[2 * i]);
+        HCUDA(cudaMemsetAsync(d.F, 0, (size_t)d.n * sizeof(uint64_t), s));
+        HCUDA(cudaMemsetAsync(d.R, 0, (size_t)d.n * sizeof(uint32_t), s));
     }
 
     const size_t words = (size_t)maxn * W * nteams;
@@ -920,13 +974,42 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     A.stats = stats ? st.p : nullptr;
     void *args[] = {&A};
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
-    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
+    if (!plain) {
+        g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+        HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
+    } else {
+        // plain schedule: one launch per phase, the host reads the level counters after every level
+        uint32_t ps = 0;
+        for (size_t gi = 0; gi < ng; ++gi) {
+            for (int32_t b = 0; b < desc[gi].nbatches; ++b) {
+                const int32_t s0 = b * 64 * W, ns = std::min(64 * W, desc[gi].n - s0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, 1, ps, 0);
+                ++ps;
+                int32_t cur_a = 1;
+                for (int32_t level = 2; level <= desc[gi].n + 1; ++level) {
+                    unsigned long long h3[3];
+                    HCUDA(cudaMemcpyAsync(h3, ctr.p + 4 * ((ps - 1) % 3), sizeof(h3), cudaMemcpyDeviceToHost, s));
+                    HCUDA(cudaStreamSynchronize(s));
+                    if (h3[0] == 0) break;
+                    if ((unsigned long long)A.push_alpha * h3[1] < h3[2]) {
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_PUSH, s0, ns, level, ps, cur_a);
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, level, ps,
+                               cur_a);
+                    } else {
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_PULL, s0, ns, level, ps, cur_a);
+                    }
+                    ++ps;
+                    cur_a ^= 1;
+                }
+            }
+        }
+    }
     if (ev_stop) HCUDA(cudaEventRecord(ev_stop, s));
-    if (t.relabel)
-        for (size_t i = 0; i < ng; ++i)
-            launch(k_scatter_back, (unsigned)ceil_div(desc[i].n, 256), 256, 0, s, desc[i].n, perm[i].p, Fi[i].p,
-                   Ri[i].p, jobs[i].F, jobs[i].R);
+    for (size_t i = 0; i < ng; ++i)
+        if (jobs[i].g->relabeled)
+            launch(k_scatter_back, (unsigned)ceil_div(desc[i].n, 256), 256, 0, s, desc[i].n, jobs[i].g->perm.p,
+                   (const uint64_t *)Fi[i].p, (const uint32_t *)Ri[i].p, jobs[i].F, jobs[i].R);
     HCUDA(cudaGetLastError());
     if (stats) {
         unsigned long long h[ST_N];
@@ -947,11 +1030,19 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     }
 }
 
-void msbfs_all_sources(const Csr &g, uint64_t *d_F, uint32_t *d_R, const BfsTuning &t, int32_t *d_err, Alloc *al,
-                       cudaStream_t s, BfsStats *stats, float *kernel_ms, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
-    (void)kernel_ms;
-    std::vector<BfsJob> jobs{BfsJob{&g, d_F, d_R}};
-    msbfs_multi(jobs, t, d_err, al, s, stats, ev_start, ev_stop);
+void bfs_prepare(const Csr &g, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s) {
+    out.relabeled = relabel;
+    if (relabel) {
+        relabel_by_degree(g, out.csr, out.perm, al, s);
+    } else {  // the BFS reads the graph as it is
+        out.csr.n = g.n;
+        out.csr.nnz = g.nnz;
+        if (!out.csr.rowptr.alloc(al, (size_t)g.n + 1) || !out.csr.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
+            fail(HOMLN_ENOMEM, "bfs graph");
+        HCUDA(cudaMemcpyAsync(out.csr.rowptr.p, g.rowptr.p, sizeof(int64_t) * (g.n + 1), cudaMemcpyDeviceToDevice, s));
+        if (g.nnz > 0)
+            HCUDA(cudaMemcpyAsync(out.csr.col.p, g.col.p, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToDevice, s));
+    }
 }
 
 }  // namespace homln

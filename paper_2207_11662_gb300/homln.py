@@ -32,7 +32,7 @@ EXPORTS = [
     "homln_create", "homln_destroy", "homln_set_tuning", "homln_layer_closeness", "homln_and_aggregate",
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
-    "homln_version", "homln_accuracy_noalloc", "homln_analyse",
+    "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
 ]
 
 
@@ -52,7 +52,7 @@ class homln_accuracy_t(ctypes.Structure):
 class homln_tuning(ctypes.Structure):
     _fields_ = [("words_per_node", c_int32), ("push_alpha", c_int32), ("threads", c_int32),
                 ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("team_mix", c_int32),
-                ("reserved", c_int32 * 1)]
+                ("schedule", c_int32)]
 
 
 class homln_profile_t(ctypes.Structure):
@@ -92,6 +92,7 @@ def _load():
         "homln_set_tuning": (S, [c_void_p, POINTER(homln_tuning)]),
         "homln_layer_closeness": (S, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
         "homln_analyse": (S, [c_void_p, c_uint64, c_int32]),
+        "homln_batch_analyse": (S, [POINTER(c_void_p), c_int32, POINTER(c_uint64), c_int32]),
         "homln_and_aggregate": (S, [c_void_p, c_uint64, c_int64, c_void_p, c_void_p, POINTER(c_int64)]),
         "homln_and_closeness": (S, [c_void_p, c_uint64, c_void_p, c_void_p, c_void_p]),
         "homln_topk": (S, [c_void_p, c_int32, c_uint64, POINTER(homln_select), c_void_p, POINTER(c_int32)]),
@@ -102,6 +103,7 @@ def _load():
         "homln_reset_profile": (S, [c_void_p]),
         "homln_kernel_launches": (c_int64, []),
         "homln_sync": (S, [c_void_p]),
+        "homln_invalidate": (S, [c_void_p]),
         "homln_last_error": (c_char_p, []),
         "homln_version": (c_char_p, []),
         "homln_accuracy_noalloc": (S, [c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
@@ -188,13 +190,20 @@ def homln_destroy(h) -> None:
 
 
 def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0,
-                     team_mix=0) -> None:
-    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix)
+                     team_mix=0, schedule=0) -> None:
+    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix, schedule)
     _check(lib.homln_set_tuning(h, ctypes.byref(t)), "homln_set_tuning")
 
 
 def homln_analyse(h, layer_mask: int, with_and: bool = True) -> None:
     _check(lib.homln_analyse(h, int(layer_mask), int(bool(with_and))), "homln_analyse")
+
+
+def homln_batch_analyse(handles, masks, with_and: bool = True) -> None:
+    n = len(handles)
+    hs = (c_void_p * n)(*handles)
+    ms = (c_uint64 * n)(*[int(m) for m in masks])
+    _check(lib.homln_batch_analyse(hs, n, ms, int(bool(with_and))), "homln_batch_analyse")
 
 
 def homln_layer_closeness(h, layer: int, farness=None, reach=None, cc=None) -> None:
@@ -258,6 +267,10 @@ def homln_reset_profile(h) -> None:
 
 def homln_kernel_launches() -> int:
     return int(lib.homln_kernel_launches())
+
+
+def homln_invalidate(h) -> None:
+    _check(lib.homln_invalidate(h), "homln_invalidate")
 
 
 def homln_sync(h) -> None:

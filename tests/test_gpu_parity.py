@@ -129,6 +129,39 @@ def test_batched_analyse_and_teams(H, teams, mix):
     g.close()
 
 
+def test_plain_schedule(H):
+    """The plain schedule (one launch per phase, host-driven levels) gives the same answers."""
+    net = synth.homln_small_overlap(3000, 8.0, 3, 0.5, 41)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    for W in (2, 8):
+        g = H.Network(net.n, to_dev(net.layers), tuning=dict(schedule=1, words_per_node=W))
+        for i in range(3):
+            check_graph(*g.layer_closeness(i), ref.layer(i))
+        check_graph(*g.and_closeness(7), ref.and_graph(7))
+        g.close()
+
+
+def test_batch_analyse_across_handles(H):
+    """Many HoMLNs of uneven sizes (and streams) in one persistent launch; then invalidate and redo."""
+    import torch
+    nets = synth.homln_batch(count=6, seed=77, n_range=(300, 4000), layer_range=(2, 4))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    gs = [H.Network(net.n, to_dev(net.layers), stream=streams[i % 2].cuda_stream) for i, net in enumerate(nets)]
+    masks = [(1 << net.n_layers) - 1 for net in nets]
+    for rep in range(2):
+        H.homln_batch_analyse([g.h for g in gs], masks, True)
+        for g, net, mask in zip(gs, nets, masks):
+            ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+            with torch.cuda.stream(torch.cuda.ExternalStream(g.stream)):
+                for i in range(net.n_layers):
+                    check_graph(*g.layer_closeness(i), ref.layer(i))
+                check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+        for g in gs:
+            H.homln_invalidate(g.h)
+    for g in gs:
+        g.close()
+
+
 def test_hubs_use_block_and_warp_tiers(H):
     """A star plus a power-law layer: the centre's row exceeds the block threshold."""
     n = 5000
