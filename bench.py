@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--team-mix", type=int, default=0, help="1: blocks on one SM join different teams")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-seconds", type=float, default=15.0)
+    p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--single-bfs", action="store_true",
                    help="profiling aid: build the workload, run one layer's all-sources BFS once, exit")
     p.add_argument("--launch-list", action="store_true",
@@ -405,6 +408,39 @@ def batch_vs_plain(args, dev):
             "autotune_candidates_ms": tune_log["candidates"]}
 
 
+def _serving_item(arg):
+    """Spawn-pool worker: one request's HoMLN (raw edge lists) and its TEPS work."""
+    i, spec, arrival = arg
+    from paper_2207_11662_gb300 import synth
+    net = synth.build_request(spec, raw=True)
+    work, _ = teps_work(net.n, net.layers)
+    return i, net.n, net.layers, arrival, work
+
+
+def serving(args, dev):
+    """Poisson stream (mean 50 req/s) of closeness/top-k queries on HoMLNs of 2-6 layers and
+    1,000-100,000 nodes (log-uniform), ER or power-law layers of average degree 6-12, served by the
+    continuous-batching server; latency = completion - arrival."""
+    import multiprocessing as mp
+    from paper_2207_11662_gb300 import serve
+    from paper_2207_11662_gb300 import synth
+    specs = synth.serving_requests(duration_s=args.serve_seconds, rate=args.serve_rate, seed=5001)
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        items = pool.map(_serving_item, [(i, r["spec"], r["t"]) for i, r in enumerate(specs)], chunksize=4)
+    reqs = [serve.Request(i, n, layers, arrival=t, teps_work=w) for i, n, layers, t, w in items]
+    srv = serve.Server(device=dev.index or 0, workers=3, max_wave=16, mem_budget_bytes=32 << 30)
+    t0 = time.perf_counter()
+    done = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    out = serve.latency_stats(done, wall)
+    out.update({"duration_s": round(wall, 2), "rate_req_per_s": args.serve_rate, "workers": 3, "max_wave": 16,
+                "waves": srv.waves, "errors": srv.errors[:3],
+                "workload": "Poisson arrivals, HoMLNs of 2-6 layers, n log-uniform in [1e3, 1e5], ER or "
+                            "Chung-Lu layers (avg deg 6-12); per request: Psi of all layers + AND, top-10% ground "
+                            "truth, CC2 estimate and its accuracy"})
+    return out
+
+
 def cpu_baseline(net, sources_per_graph: int, seed: int = 2001):
     """The oracle as it stands: queue BFS from a seeded sample of sources on every analysed graph."""
     from oracle import oracle as O
@@ -461,9 +497,12 @@ def main():
     if result is None:
         return
     if rank == 0:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
         if not args.no_batch:
-            import torch
-            result["batched_vs_plain"] = batch_vs_plain(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+            result["batched_vs_plain"] = batch_vs_plain(args, dev)
+        if not args.no_serve and world == 1:
+            result["serving"] = serving(args, dev)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)
         print(json.dumps(result))

@@ -283,9 +283,35 @@ def serving_requests(duration_s: float = 60.0, rate: float = 50.0, seed: int = 5
     return reqs
 
 
-def build_request(spec) -> HoMLN:
+def _raw_er(n: int, m: int, rng):
+    return rng.integers(0, n, size=m).astype(np.int32), rng.integers(0, n, size=m).astype(np.int32)
+
+
+def _raw_cl(n: int, m: int, cdf, rng):
+    a = np.searchsorted(cdf, rng.random(m), side="right").clip(0, n - 1).astype(np.int32)
+    b = np.searchsorted(cdf, rng.random(m), side="right").clip(0, n - 1).astype(np.int32)
+    return a, b
+
+
+def build_request(spec, raw: bool = False) -> HoMLN:
+    """The HoMLN of one serving request. raw=True samples endpoints without removing self loops
+    or repeated pairs (the library normalises its input), which is much faster to generate."""
     kind, n, L, deg, s = spec
     m = int(deg * n / 2)
+    if raw:
+        rng = _rng(s)
+        if kind == "er":
+            layers = [_raw_er(n, m, rng) for _ in range(L)]
+        else:
+            w = chung_lu_weights(n, deg, 2.5)
+            cdf = np.cumsum(w)
+            cdf /= cdf[-1]
+            pool = _raw_cl(n, m // 2, cdf, rng)
+            layers = []
+            for _ in range(L):
+                own = _raw_cl(n, m - m // 2, cdf, rng)
+                layers.append((np.concatenate([pool[0], own[0]]), np.concatenate([pool[1], own[1]])))
+        return HoMLN(n, layers, name=f"req{s}", meta={"kind": kind, "deg": deg, "raw": True})
     if kind == "er":
         layers = [er_edges(n, m, s * 8 + i) for i in range(L)]
     else:
