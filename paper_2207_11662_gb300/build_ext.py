@@ -39,8 +39,19 @@ def sources():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Build the library. HOMLN_NVCC_EXTRA (environment) adds nvcc flags, e.g. the kernel's
+    compile-time knobs -DHOMLN_GATHER_UNROLL=8 or -DHOMLN_BFS_MIN_BLOCKS=3; a change of
+    these flags rebuilds everything."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
+    extra = os.environ.get("HOMLN_NVCC_EXTRA", "").split()
+    stamp = os.path.join(BUILD, "flags.txt")
+    want = " ".join(ARCH + NVCC_FLAGS + extra)
+    try:
+        with open(stamp) as f:
+            force = force or f.read() != want
+    except OSError:
+        force = True
     newest_header = max(os.path.getmtime(h) for h in _headers())
     jobs = []
     for src in sources():
@@ -52,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         src, obj, stale = job
         if not stale:
             return None
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             return f"{' '.join(cmd)}\n{r.stdout}\n{r.stderr}"
@@ -73,6 +84,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(want)
     return LIB
 
 

@@ -209,52 +209,56 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b, uint64_t limit_n
     return s_ok != 0;
 }
 
+#ifndef HOMLN_GATHER_UNROLL
+#define HOMLN_GATHER_UNROLL 4
+#endif
+#ifndef HOMLN_BFS_MIN_BLOCKS
+#define HOMLN_BFS_MIN_BLOCKS 2
+#endif
+constexpr int kUnroll = HOMLN_GATHER_UNROLL;
+
 // OR the frontier words (this lane's K of them) of neighbours rb+p, rb+p+S, ... into acc;
-// stop once every bit this lane still needs is present. The next four column indices
-// are loaded while the current four frontier words are in flight. Returns neighbours visited.
+// stop once every bit this lane still needs is present. kUnroll neighbours are gathered per
+// step (past the row end the loads are predicated off), and the column indices of the next
+// step are loaded while the current frontier words are in flight. Returns neighbours visited.
 template <int W>
 __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__restrict__ cur, int64_t rb, int64_t re,
                                              int p, int S, int q, const uint64_t (&need)[Geo<W>::K],
                                              uint64_t (&acc)[Geo<W>::K]) {
-    constexpr int K = Geo<W>::K;
-    const int64_t S4 = 4 * (int64_t)S;
+    constexpr int K = Geo<W>::K, U = kUnroll;
     int64_t j = rb + p;
+    if (j >= re) return 0;
     int64_t it = 0;
-    if (j + 3 * (int64_t)S < re) {
-        int32_t u0 = __ldg(a.col + j), u1 = __ldg(a.col + j + S), u2 = __ldg(a.col + j + 2 * S),
-                u3 = __ldg(a.col + j + 3 * S);
-        while (true) {
-            uint64_t f0[K], f1[K], f2[K], f3[K];
-            ldw<K>(cur + (int64_t)u0 * W + q * K, f0);
-            ldw<K>(cur + (int64_t)u1 * W + q * K, f1);
-            ldw<K>(cur + (int64_t)u2 * W + q * K, f2);
-            ldw<K>(cur + (int64_t)u3 * W + q * K, f3);
-            const int64_t jn = j + S4;
-            const bool more = jn + 3 * (int64_t)S < re;
-            if (more) {
-                u0 = __ldg(a.col + jn);
-                u1 = __ldg(a.col + jn + S);
-                u2 = __ldg(a.col + jn + 2 * S);
-                u3 = __ldg(a.col + jn + 3 * S);
+    int32_t u[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) u[i] = (j + (int64_t)i * S < re) ? __ldg(a.col + j + (int64_t)i * S) : -1;
+    while (true) {
+        uint64_t f[U][K];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if (u[i] >= 0) {
+                ldw<K>(cur + (int64_t)u[i] * W + q * K, f[i]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) f[i][k] = 0;
             }
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] |= f0[k] | f1[k] | f2[k] | f3[k];
-            it += 4;
-            j = jn;
-            if (covers<K>(acc, need)) return it;
-            if (!more) break;
         }
-    }
-    for (; j < re; j += S) {
-        const int32_t u = __ldg(a.col + j);
-        uint64_t f[K];
-        ldw<K>(cur + (int64_t)u * W + q * K, f);
+        const int64_t jn = j + (int64_t)U * S;
+        const bool more = jn < re;
+        const int64_t here = (min(re, jn) - j + S - 1) / S;
+        if (more) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] |= f[k];
-        ++it;
+            for (int i = 0; i < U; ++i) u[i] = (jn + (int64_t)i * S < re) ? __ldg(a.col + jn + (int64_t)i * S) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] |= f[i][k];
+        it += here;
         if (covers<K>(acc, need)) return it;
+        if (!more) return it;
+        j = jn;
     }
-    return it;
 }
 
 struct PhaseCounters {
@@ -664,7 +668,7 @@ __device__ __forceinline__ uint32_t sm_id() {
 }
 
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
+__global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A) {
     PhaseCounters c;
     unsigned long long st[ST_N];
 #pragma unroll
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(512, 2) k_msbfs(TeamArgs A) {
 enum PhaseKind { PH_START = 0, PH_FINALIZE = 1, PH_PULL = 2, PH_PUSH = 3 };
 
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512, 2) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
+__global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
                                                   int32_t level, uint32_t ps, int32_t cur_is_a) {
     PhaseCounters c;
     unsigned long long st[ST_N];
@@ -852,7 +856,7 @@ BfsKernel kernel_for(int W, bool stats) {
 // 8 teams x W=8 and 4 teams x W=16 (both 102 MB) beat every 51 MB split, so the budget
 // lets the state exceed L2 a little; the frontier gathers still mostly hit in L2.
 constexpr double kStateBudget = 104.0e6;
-constexpr int kDefaultTeams = 8;
+constexpr int kMaxTeams = 16;
 
 }  // namespace
 
@@ -879,16 +883,20 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
 
     const bool plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
-    int nteams = plain ? 1 : (t.teams > 0 ? t.teams : kDefaultTeams);
-    int W = t.W;
-    if (W <= 0) {
-        W = msbfs_pick_words(maxn, maxnnz);
-        while (W > 1 && nteams * 4.0 * maxn * 8.0 * W > kStateBudget) W >>= 1;
-    }
-    if (t.teams <= 0 && !plain) {  // no more teams than tiles
-        int64_t tiles = 0;
-        for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
-        if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
+    // Defaults, measured on GB300: 8 words per node (512 sources per tile) with as many teams as
+    // the state budget allows, at most 16 (8 teams at n = 50,000, 2 at n = 200,000).
+    int W = t.W > 0 ? t.W : std::min(8, msbfs_pick_words(maxn, maxnnz));
+    int nteams = 1;
+    if (!plain) {
+        if (t.teams > 0) {
+            nteams = t.teams;
+        } else {
+            nteams = (int)std::floor(kStateBudget / (4.0 * maxn * 8.0 * W));
+            nteams = std::max(1, std::min(kMaxTeams, nteams));
+            int64_t tiles = 0;  // no more teams than tiles
+            for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
+            if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
+        }
     }
     const int T = W >= 2 ? W / 2 : 1;
 
