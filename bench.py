@@ -59,14 +59,31 @@ def parse():
     return p.parse_args()
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank analyses its own HoMLN (replicas, weak scaling): same shape, its own seed."""
+    return base + 7919 * rank
+
+
+def job_aggregate(units: float, seconds: float, dist=None, device=None):
+    """Whole-job throughput inputs: units summed over ranks, time = the slowest rank's."""
+    if dist is None:
+        return units, seconds
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def make_workload(name: str, rank: int):
     from paper_2207_11662_gb300 import synth
     if name == "powerlaw50k":
-        net = synth.homln_powerlaw(n=50000, avg_deg=10.0, n_layers=4, gamma=2.5, seed=2001 + 7919 * rank)
+        net = synth.homln_powerlaw(n=50000, avg_deg=10.0, n_layers=4, gamma=2.5, seed=replica_seed(2001, rank))
         desc = (f"4 Chung-Lu layers (gamma 2.5, avg deg 10), n=50000, shared pool rho={net.meta['rho']:.3f}; "
                 "per-layer + AND all-sources closeness, top-10%, naive/CC1/CC2, accuracy")
     elif name == "ba200k":
-        net = synth.homln_ba_large(n=200000, m_attach=4, n_layers=4, seed=4001 + 7919 * rank)
+        net = synth.homln_ba_large(n=200000, m_attach=4, n_layers=4, seed=replica_seed(4001, rank))
         desc = "4 BA layers (m=4), n=200000, ~50% shared edges; full hot path"
     else:
         net = synth.homln_small_er(seeds=(101 + rank, 102 + rank, 103 + rank))
@@ -164,6 +181,30 @@ def peaks():
             p = json.load(f)
         return float(p["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def measured_traffic(workload: str, tiles: int):
+    """DRAM bytes per BFS launch from the committed ncu summary (profiles/), scaled from the captured
+    tiles to this launch's tiles; None when the kernel source changed since the counters were taken."""
+    import hashlib
+    if workload != "powerlaw50k":
+        return None
+    path = os.path.join(ROOT, "profiles", "k_msbfs_powerlaw50k_layer.md")
+    src = os.path.join(ROOT, "paper_2207_11662_gb300", "csrc", "msbfs.cu")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("|", "#", "`")):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if kv.get("kernel_source_sha256_16") != sha:
+            return None
+        return int(int(kv["dram_bytes_per_tile"]) * tiles)
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def bfs_bytes(prof: dict) -> float:
@@ -274,13 +315,9 @@ def run_ours(args, rank, world, dist):
     launches = H.homln_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(step_ms) / 1000.0
+    units, t_max = job_aggregate(work * args.steps, t_local, dist, dev)
     if dist:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        t_max = float(t.item())
-    else:
-        t_max = t_local
     torch.cuda.synchronize()
 
     # end to end through the C-ABI with host buffers: pinned inputs, H2D + D2H inside the timed region
@@ -317,7 +354,8 @@ def run_ours(args, rank, world, dist):
                    "teps_edges_per_step": work, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world} (one HoMLN per GPU)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / hbm, 4),
+                     "traffic": measured_traffic(args.workload, prof_count["batches"]), "peak_kind": peak_kind,
                      "kernel": "k_msbfs (persistent all-sources BFS, one launch per graph)",
                      "algorithmic_bytes_per_launch": round(alg_bytes_per_launch),
                      "launch_ms": round(bfs_ms / max(bfs_launches, 1), 4),
@@ -333,7 +371,7 @@ def run_ours(args, rank, world, dist):
                                                    "words_pushed", "bytes", "visits", "words_per_node",
                                                    "teams")},
     }
-    result["value"] = round(work * world * args.steps / t_max / 1e9, 3)
+    result["value"] = round(units / t_max / 1e9, 3)
     return result, net
 
 
@@ -499,7 +537,7 @@ def main():
     if rank == 0:
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-        if not args.no_batch:
+        if not args.no_batch and world == 1:
             result["batched_vs_plain"] = batch_vs_plain(args, dev)
         if not args.no_serve and world == 1:
             result["serving"] = serving(args, dev)

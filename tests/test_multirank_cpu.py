@@ -1,0 +1,40 @@
+"""The multi-rank path of bench.py on CPU: world_size 2 over gloo, 127.0.0.1.
+
+Each rank analyses its own HoMLN (replicas); the job's throughput is the units summed over the
+ranks divided by the slowest rank's time. No data-path collective is involved."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    units, secs = bench.job_aggregate(100.0 * (rank + 1), 1.0 + rank, dist, "cpu")
+    seeds = [None] * world
+    dist.all_gather_object(seeds, bench.replica_seed(2001, rank))
+    out[rank] = (units, secs, seeds)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation_gloo():
+    import torch.multiprocessing as mp
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+        res = dict(out)
+    for r in range(world):
+        units, secs, seeds = res[r]
+        assert units == 300.0 and secs == 2.0  # summed work, slowest rank's time
+        assert len(set(seeds)) == world  # every rank analyses its own HoMLN
