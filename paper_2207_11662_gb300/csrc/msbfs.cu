@@ -215,6 +215,15 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b, uint64_t limit_n
 #ifndef HOMLN_BFS_MIN_BLOCKS
 #define HOMLN_BFS_MIN_BLOCKS 2
 #endif
+#ifndef HOMLN_WARP_COORD
+#define HOMLN_WARP_COORD 1
+#endif
+#ifndef HOMLN_WARP_TIER_ITERS
+#define HOMLN_WARP_TIER_ITERS 4
+#endif
+#ifndef HOMLN_BLOCK_TIER_ITERS
+#define HOMLN_BLOCK_TIER_ITERS 4
+#endif
 constexpr int kUnroll = HOMLN_GATHER_UNROLL;
 
 // OR the frontier words (this lane's K of them) of neighbours rb+p, rb+p+S, ... into acc;
@@ -259,6 +268,43 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
         if (!more) return it;
         j = jn;
     }
+}
+
+// The warp-tier gather: the 32/T slots of one warp take every (32/T)-th neighbour of the
+// same row; after each step their partial results are OR-ed across the warp, so all slots
+// stop as soon as the row as a whole has supplied every missing bit (early exit for the whole
+// row, not per slot). Every lane of the warp calls it. Returns the combined OR.
+template <int W>
+__device__ __forceinline__ int64_t gather_or_warp(const Tile &a, const uint64_t *__restrict__ cur, int64_t rb,
+                                                  int64_t re, int q, const uint64_t (&need)[Geo<W>::K],
+                                                  uint64_t (&acc)[Geo<W>::K]) {
+    constexpr int K = Geo<W>::K, T = Geo<W>::T, S = 32 / T, U = kUnroll;
+    const int p = (threadIdx.x & 31) / T;
+    int64_t it = 0;
+    for (int64_t j = rb + p; __any_sync(0xffffffffu, j < re); j += (int64_t)U * S) {
+        uint64_t f[U][K];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int64_t jj = j + (int64_t)i * S;
+            if (jj < re) {
+                ldw<K>(cur + (int64_t)__ldg(a.col + jj) * W + q * K, f[i]);
+                ++it;
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) f[i][k] = 0;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] |= f[i][k];
+#pragma unroll
+        for (int o = T; o < 32; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] |= __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (__all_sync(0xffffffffu, covers<K>(acc, need))) break;
+    }
+    return it;
 }
 
 struct PhaseCounters {
@@ -508,7 +554,11 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             const bool full0 = !__any_sync(0xffffffffu, lane_need);
             const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
             int64_t it = 0;
+#if HOMLN_WARP_COORD
+            if (!full0) it = gather_or_warp<W>(a, cur, rb, re, q, need, acc);
+#else
             if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
+#endif
             if (STATS) {
                 st[ST_WORDS] += it * K;
                 st[ST_BYTES] += it * 8 * K;
@@ -727,8 +777,11 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         a.ctr = ctr;
         a.n = g.n;
         // hub tiers: rows of at least 4 iterations per slot go to a whole block / a whole warp
-        a.hub_block_end = g.by_degree ? first_below(g.rowptr, g.n, 4 * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
-        a.hub_warp_end = g.by_degree ? max(a.hub_block_end, first_below(g.rowptr, g.n, 4 * (32 / Geo<W>::T))) : 0;
+        a.hub_block_end =
+            g.by_degree ? first_below(g.rowptr, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+        a.hub_warp_end = g.by_degree
+                             ? max(a.hub_block_end, first_below(g.rowptr, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                             : 0;
         a.rank = rank;
         a.tsize = tsize;
         a.push_alpha = A.push_alpha;
@@ -778,8 +831,11 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.R = g.R;
     a.ctr = A.ctr;
     a.n = g.n;
-    a.hub_block_end = g.by_degree ? first_below(g.rowptr, g.n, 4 * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
-    a.hub_warp_end = g.by_degree ? max(a.hub_block_end, first_below(g.rowptr, g.n, 4 * (32 / Geo<W>::T))) : 0;
+    a.hub_block_end =
+            g.by_degree ? first_below(g.rowptr, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+    a.hub_warp_end = g.by_degree
+                         ? max(a.hub_block_end, first_below(g.rowptr, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                         : 0;
     a.rank = blockIdx.x;
     a.tsize = gridDim.x;
     a.push_alpha = A.push_alpha;
