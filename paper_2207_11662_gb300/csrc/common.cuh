@@ -176,6 +176,8 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, Alloc *al, c
 // Stable LSD radix sort of 64-bit keys on bits [bit0, bit1), optional uint32 payload.
 // Result in keys/vals (the alternate buffers are scratch).
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit1, Alloc *al, cudaStream_t s);
+// Sort every CSR row's entries ascending, in place (segmented sort).
+void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Graph building (graph.cu)

@@ -13,41 +13,71 @@ namespace {
 
 constexpr int NODE_BITS = 20;  // HOMLN_MAX_NODES = 2^20
 constexpr uint64_t NODE_MASK = (1ull << NODE_BITS) - 1;
-constexpr uint64_t KEY_SENTINEL = (1ull << (2 * NODE_BITS)) - 1;  // sorts after every real key
 
-// Each undirected input edge (a, b) becomes the directed keys a:b and b:a.
-__global__ void k_expand_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m, int32_t n,
-                               uint64_t *__restrict__ keys, int32_t *err) {
+// Degree of each endpoint of every valid, non-loop edge (both directions).
+__global__ void k_count_deg(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m, int32_t n,
+                            int32_t *__restrict__ deg, int32_t *err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = src[e], b = dst[e];
-        uint64_t k0 = KEY_SENTINEL, k1 = KEY_SENTINEL;
+        const int32_t a = src[e], b = dst[e];
         if (a < 0 || a >= n || b < 0 || b >= n) {
             dev_fail(err, DEV_BAD_ID);
-        } else if (a != b) {
-            k0 = ((uint64_t)a << NODE_BITS) | (uint64_t)b;
-            k1 = ((uint64_t)b << NODE_BITS) | (uint64_t)a;
+            continue;
         }
-        keys[2 * e] = k0;
-        keys[2 * e + 1] = k1;
+        if (a == b) continue;
+        atomicAdd(&deg[a], 1);
+        atomicAdd(&deg[b], 1);
     }
 }
 
-__global__ void k_unique_flags(const uint64_t *__restrict__ keys, int64_t cnt, int32_t *__restrict__ flag) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        flag[i] = (k != KEY_SENTINEL && (i == 0 || keys[i - 1] != k)) ? 1 : 0;
+// Each edge lands in both endpoints' rows (row order is fixed later by the row sort).
+__global__ void k_scatter_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m, int32_t n,
+                                unsigned long long *__restrict__ cursor, int32_t *__restrict__ col) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
+        col[atomicAdd(&cursor[a], 1ull)] = b;
+        col[atomicAdd(&cursor[b], 1ull)] = a;
     }
 }
 
-__global__ void k_compact_keys(const uint64_t *__restrict__ keys, const int32_t *__restrict__ flag,
-                               const int64_t *__restrict__ pos, int64_t cnt, int32_t *__restrict__ col,
-                               int32_t *__restrict__ deg) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        if (flag[i]) {
-            uint64_t k = keys[i];
-            col[pos[i]] = (int32_t)(k & NODE_MASK);
-            atomicAdd(&deg[k >> NODE_BITS], 1);
+// Warp per row of a row-sorted CSR: count (or write) the entries that differ from their predecessor.
+template <bool WRITE>
+__global__ void k_row_unique(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             int32_t *__restrict__ cnt, const int64_t *__restrict__ orp, int32_t *__restrict__ ocol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        const int64_t b = rp[r], e = rp[r + 1];
+        const int64_t o = WRITE ? orp[r] : 0;
+        int32_t c = 0;
+        for (int64_t j0 = b; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool keep = false;
+            int32_t v = 0;
+            if (j < e) {
+                v = col[j];
+                keep = (j == b) || col[j - 1] != v;
+            }
+            const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+            if (WRITE && keep) ocol[o + c + __popc(mk & ((1u << lane) - 1u))] = v;
+            c += __popc(mk);
         }
+        if (!WRITE && lane == 0) cnt[r] = c;
+    }
+}
+
+// Relabelled rows, unsorted: row i of the new graph holds inv[] of old row perm[i].
+__global__ void k_relabel_rows(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
+                               const int64_t *__restrict__ nrp, int32_t *__restrict__ ncol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int32_t old = perm[i];
+        const int64_t a = rp[old], len = rp[old + 1] - a, o = nrp[i];
+        for (int64_t j = lane; j < len; j += 32) ncol[o + j] = inv[col[a + j]];
     }
 }
 
@@ -147,27 +177,6 @@ __global__ void k_perm_from_keys(int32_t n, const uint64_t *__restrict__ keys, c
     }
 }
 
-// Relabelled entries as (new row, new col) keys; sorting them sorts every row.
-__global__ void k_relabel_entries(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                  const int32_t *__restrict__ perm, const int32_t *__restrict__ inv,
-                                  const int64_t *__restrict__ nrp, uint64_t *__restrict__ keys) {
-    // one warp per new row
-    int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < n; i += nwarps) {
-        int32_t old = perm[i];
-        int64_t a = rp[old], len = rp[old + 1] - a, o = nrp[i];
-        for (int64_t j = lane; j < len; j += 32)
-            keys[o + j] = ((uint64_t)i << NODE_BITS) | (uint64_t)inv[col[a + j]];
-    }
-}
-
-__global__ void k_keys_to_col(int64_t cnt, const uint64_t *__restrict__ keys, int32_t *__restrict__ col) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        col[i] = (int32_t)(keys[i] & NODE_MASK);
-}
-
 unsigned grid_for(int64_t work, int threads = 256) {
     int64_t b = ceil_div(work > 0 ? work : 1, threads);
     return (unsigned)(b > 65535 * 16 ? 65535 * 16 : b);
@@ -184,6 +193,8 @@ int64_t read_i64(const int64_t *d, cudaStream_t s) {
 
 void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m, Csr &out, int32_t *d_err, Alloc *al,
                cudaStream_t s) {
+    // degrees -> row offsets -> scatter both directions of every edge -> sort each row ->
+    // drop repeated entries (self loops were dropped at the scatter)
     out.n = n;
     if (!out.rowptr.alloc(al, (size_t)n + 1)) fail(HOMLN_ENOMEM, "csr rowptr");
     if (m == 0) {
@@ -192,21 +203,26 @@ void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
         out.col.release();
         return;
     }
-    const int64_t cnt = 2 * m;
-    DBuf<uint64_t> keys;
-    DBuf<int32_t> flag, deg;
-    DBuf<int64_t> pos;
-    if (!keys.alloc(al, cnt) || !flag.alloc(al, cnt) || !pos.alloc(al, cnt + 1) || !deg.alloc(al, n))
+    DBuf<int32_t> deg, raw, cnt;
+    DBuf<int64_t> rp;
+    DBuf<unsigned long long> cursor;
+    if (!deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cursor.alloc(al, n) || !raw.alloc(al, 2 * m) ||
+        !cnt.alloc(al, n))
         fail(HOMLN_ENOMEM, "csr scratch");
-    launch(k_expand_edges, grid_for(m), 256, 0, s, d_src, d_dst, m, n, keys.p, d_err);
-    radix_sort_u64(keys.p, nullptr, cnt, 0, 2 * NODE_BITS, al, s);
-    launch(k_unique_flags, grid_for(cnt), 256, 0, s, keys.p, cnt, flag.p);
-    scan_exclusive_i32(flag.p, pos.p, cnt, al, s);
-    out.nnz = read_i64(pos.p + cnt, s);
-    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "csr col");
     HCUDA(cudaMemsetAsync(deg.p, 0, sizeof(int32_t) * n, s));
-    launch(k_compact_keys, grid_for(cnt), 256, 0, s, keys.p, flag.p, pos.p, cnt, out.col.p, deg.p);
-    scan_exclusive_i32(deg.p, out.rowptr.p, n, al, s);
+    launch(k_count_deg, grid_for(m), 256, 0, s, d_src, d_dst, m, n, deg.p, d_err);
+    scan_exclusive_i32(deg.p, rp.p, n, al, s);
+    HCUDA(cudaMemcpyAsync(cursor.p, rp.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
+    launch(k_scatter_edges, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
+    sort_rows(n, rp.p, raw.p, al, s);
+    launch(k_row_unique<false>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
+           (const int32_t *)raw.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr);
+    scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
+    out.nnz = read_i64(out.rowptr.p + n, s);
+    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "csr col");
+    if (out.nnz > 0)
+        launch(k_row_unique<true>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
+               (const int32_t *)raw.p, (int32_t *)nullptr, (const int64_t *)out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
 }
 
@@ -258,12 +274,9 @@ void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, c
         fail(HOMLN_ENOMEM, "relabel csr");
     scan_exclusive_i32(newdeg.p, out.rowptr.p, n, al, s);
     if (g.nnz > 0) {
-        DBuf<uint64_t> ekeys;
-        if (!ekeys.alloc(al, g.nnz)) fail(HOMLN_ENOMEM, "relabel keys");
-        launch(k_relabel_entries, grid_for((int64_t)n * 32), 256, 0, s, n, g.rowptr.p, g.col.p, perm.p, inv.p,
-                                                                    out.rowptr.p, ekeys.p);
-        radix_sort_u64(ekeys.p, nullptr, g.nnz, 0, 2 * NODE_BITS, al, s);
-        launch(k_keys_to_col, grid_for(g.nnz), 256, 0, s, g.nnz, ekeys.p, out.col.p);
+        launch(k_relabel_rows, grid_for((int64_t)n * 32), 256, 0, s, n, g.rowptr.p, g.col.p, perm.p, inv.p,
+               out.rowptr.p, out.col.p);
+        sort_rows(n, out.rowptr.p, out.col.p, al, s);
     }
     HCUDA(cudaGetLastError());
 }

@@ -3,6 +3,9 @@
 // selection. Hand-written; no library kernels.
 #include "common.cuh"
 
+#include <algorithm>
+#include <climits>
+
 namespace homln {
 
 namespace {
@@ -205,6 +208,94 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Segmented sort of CSR rows (each row ascending, in place).
+// Rows of <= 32 entries: one warp, a bitonic network in registers. Rows of
+// 33 .. kRowSortSmem entries: one block, a bitonic network in shared memory.
+// Longer rows (rare: hubs of very large graphs) are collected and sorted one by
+// one with the radix sort.
+// ---------------------------------------------------------------------------
+constexpr int kRowSortSmem = 8192;
+
+__device__ __forceinline__ int32_t warp_bitonic_sort(int32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+            const bool up = (lane & k) == 0;
+            const bool lower = (lane & j) == 0;
+            x = (lower == up) ? min(x, y) : max(x, y);
+        }
+    }
+    return x;
+}
+
+__global__ void k_sort_rows_small(int32_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        const int64_t b = rp[r], d = rp[r + 1] - b;
+        if (d < 2 || d > 32) continue;  // uniform over the warp
+        int32_t x = lane < d ? col[b + lane] : INT32_MAX;
+        x = warp_bitonic_sort(x);
+        if (lane < d) col[b + lane] = x;
+    }
+}
+
+// One block per row of 33 .. kRowSortSmem entries; rows longer than that are listed in big[].
+__global__ void __launch_bounds__(256) k_sort_rows_mid(int32_t n, const int64_t *__restrict__ rp,
+                                                       int32_t *__restrict__ col, int32_t *big, int32_t *nbig) {
+    __shared__ int32_t sh[kRowSortSmem];
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t b = rp[r], d = rp[r + 1] - b;
+        if (d <= 32) continue;  // uniform over the block
+        if (d > kRowSortSmem) {
+            if (threadIdx.x == 0) big[atomicAdd(nbig, 1)] = (int32_t)r;
+            continue;
+        }
+        int P = 64;
+        while (P < d) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < d ? col[b + i] : INT32_MAX;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const int32_t x = sh[i], y = sh[l];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            sh[i] = y;
+                            sh[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < d; i += blockDim.x) col[b + i] = sh[i];
+        __syncthreads();
+    }
+}
+
+__global__ void k_i32_to_u64(int64_t cnt, const int32_t *__restrict__ a, uint64_t *__restrict__ k) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        k[i] = (uint64_t)(uint32_t)a[i];
+}
+
+__global__ void k_u64_to_i32(int64_t cnt, const uint64_t *__restrict__ k, int32_t *__restrict__ a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)k[i];
+}
+
+unsigned grid_of(int64_t work, int threads) {
+    int64_t b = ceil_div(work > 0 ? work : 1, threads);
+    return (unsigned)(b > 65535 * 16 ? 65535 * 16 : b);
+}
+
 }  // namespace
 
 void scan_exclusive_i32(const int32_t *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) {
@@ -244,6 +335,34 @@ void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit
         HCUDA(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         if (vals) HCUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
+}
+
+void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cudaStream_t s) {
+    if (n <= 0) return;
+    DBuf<int32_t> big, nbig;
+    if (!big.alloc(al, n) || !nbig.alloc(al, 1)) fail(HOMLN_ENOMEM, "row sort scratch");
+    HCUDA(cudaMemsetAsync(nbig.p, 0, sizeof(int32_t), s));
+    launch(k_sort_rows_small, grid_of((int64_t)n * 32, 256), 256, 0, s, n, d_rowptr, d_col);
+    launch(k_sort_rows_mid, (unsigned)std::min<int64_t>(n, 65535 * 4), 256, 0, s, n, d_rowptr, d_col, big.p, nbig.p);
+    int32_t h_nbig = 0;
+    HCUDA(cudaMemcpyAsync(&h_nbig, nbig.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaStreamSynchronize(s));
+    if (h_nbig == 0) return;
+    std::vector<int32_t> rows(h_nbig);
+    std::vector<int64_t> bounds(2);
+    HCUDA(cudaMemcpyAsync(rows.data(), big.p, sizeof(int32_t) * h_nbig, cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaStreamSynchronize(s));
+    for (int32_t r : rows) {
+        HCUDA(cudaMemcpyAsync(bounds.data(), d_rowptr + r, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HCUDA(cudaStreamSynchronize(s));
+        const int64_t b = bounds[0], d = bounds[1] - bounds[0];
+        DBuf<uint64_t> keys;
+        if (!keys.alloc(al, d)) fail(HOMLN_ENOMEM, "row sort keys");
+        launch(k_i32_to_u64, grid_of(d, 256), 256, 0, s, d, (const int32_t *)(d_col + b), keys.p);
+        radix_sort_u64(keys.p, nullptr, d, 0, 32, al, s);
+        launch(k_u64_to_i32, grid_of(d, 256), 256, 0, s, d, (const uint64_t *)keys.p, d_col + b);
+    }
+    HCUDA(cudaGetLastError());
 }
 
 }  // namespace homln

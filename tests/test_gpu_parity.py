@@ -174,6 +174,17 @@ def test_hubs_use_block_and_warp_tiers(H):
         full_parity(H, net, sel, tuning=dict(words_per_node=W, threads=256))
 
 
+def test_rows_longer_than_the_shared_memory_sort(H):
+    """A star whose centre row (19,999 entries) is longer than the block sort's 8,192: the CSR build
+    and the relabelling sort it with the radix-sort fallback; plus duplicates in every row."""
+    n = 20000
+    star = (np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32))
+    noisy = synth.noisy_copy(n, star, 5, self_loops=50, duplicates=3000)
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    full_parity(H, synth.HoMLN(n, [noisy, synth.overlay(n, star, synth.er_edges(n, 30000, 6))]), sel,
+                heuristics=(0, 2))
+
+
 def test_degenerate_graphs(H):
     sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)),
            (H.make_select(H.HOMLN_GE_MEAN), O.Select(O.GE_MEAN))]
