@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-paper-like", action="store_true", help="skip the paper-shaped accuracy/timing runs")
     p.add_argument("--serve-seconds", type=float, default=15.0)
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--single-bfs", action="store_true",
@@ -446,6 +447,59 @@ def batch_vs_plain(args, dev):
             "autotune_candidates_ms": tune_log["candidates"]}
 
 
+def paper_like(args, dev):
+    """Two-layer HoMLNs shaped like the paper's synthetic sets (Section 6, Table 1; seeded R-MAT
+    layers over a shared |V|-edge backbone): mean accuracy of naive, CC1 and CC2 against the AND
+    ground truth with above-average CC nodes (Tables 2-5), and the timing comparison of Section 6.1
+    (largest composition time vs smallest layer-analysis time)."""
+    import torch
+    from paper_2207_11662_gb300 import homln as H
+    from paper_2207_11662_gb300 import synth
+    stream = torch.cuda.current_stream(dev)
+    sets = {"S-1": (("powerlaw", "normal"), [(50000, 250000), (100000, 1000000)]),
+            "S-2": (("powerlaw", "powerlaw"), [(50000, 250000)]),
+            "S-3": (("normal", "normal"), [(50000, 250000)])}
+    sel = H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=0.5)
+    names = {"naive": H.HOMLN_NAIVE, "cc1": H.HOMLN_CC1, "cc2": H.HOMLN_CC2}
+    out = {}
+    psi_min, theta_max = float("inf"), {k: 0.0 for k in names}
+    seed = 6001
+    for sname, (kinds, bases) in sets.items():
+        accs = {k: [] for k in names}
+        for n, m in bases:
+            for split in ((0.7, 0.3), (0.6, 0.4), (0.5, 0.5)):
+                seed += 1
+                net = synth.homln_parmat_like(n, m, split, kinds, seed)
+                h = H.homln_create(n, [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev))
+                                       for s, d in net.layers], stream=stream.cuda_stream)
+                F = torch.empty(n, dtype=torch.int64, device=dev)
+                for i in range(2):  # Psi of each layer, timed alone
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    H.homln_layer_closeness(h, i, F, None, None)
+                    e1.record(stream)
+                    e1.synchronize()
+                    psi_min = min(psi_min, e0.elapsed_time(e1))
+                gt = np.empty(n, np.int32)
+                cg = H.homln_topk(h, -1, 3, sel, gt)
+                est = np.empty(n, np.int32)
+                for k, heur in names.items():
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    c = H.homln_compose(h, 3, heur, sel, est)
+                    theta_max[k] = max(theta_max[k], (time.perf_counter() - t0) * 1000.0)
+                    accs[k].append(H.homln_accuracy(h, est, c, gt, cg))
+                H.homln_destroy(h)
+        out[sname] = {k: {m_: round(100.0 * statistics.mean(a[m_] for a in v), 2)
+                          for m_ in ("jaccard", "precision", "recall", "f1")} for k, v in accs.items()}
+    out["min_psi_ms"] = round(psi_min, 3)
+    out["max_theta_ms"] = {k: round(v, 3) for k, v in theta_max.items()}
+    out["max_theta_over_min_psi"] = {k: round(v / psi_min, 3) for k, v in theta_max.items()}
+    out["note"] = ("accuracy in percent (Jaccard is the paper's 'accuracy'); paper (Table 2) S-1/S-2/S-3 mean "
+                   "Jaccard CC1 43.56/55.95/48.87, CC2 46.77/55.20/50.90 on PaRMAT data, context only")
+    return out
+
+
 def _serving_item(arg):
     """Spawn-pool worker: one request's HoMLN (raw edge lists) and its TEPS work."""
     i, spec, arrival = arg
@@ -541,6 +595,8 @@ def main():
             result["batched_vs_plain"] = batch_vs_plain(args, dev)
         if not args.no_serve and world == 1:
             result["serving"] = serving(args, dev)
+        if not args.no_paper_like and world == 1:
+            result["paper_like"] = paper_like(args, dev)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)
         print(json.dumps(result))

@@ -210,6 +210,24 @@ HOMLN_API homln_status homln_topk(homln_t h, int32_t which, uint64_t layer_mask,
 HOMLN_API homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, const homln_select *sel,
                            int32_t *nodes_out, int32_t *count_out);
 
+/* One subset of layers in homln_subset_sweep. */
+typedef struct homln_subset_result {
+    uint64_t mask;          /* the subset (bit i = layer i) */
+    int32_t truth_count;    /* ground-truth CC nodes (AND graph of the subset) */
+    int32_t estimate_count; /* CC nodes estimated by the heuristic from the layers' partial results */
+    homln_accuracy_t acc;   /* estimate vs ground truth */
+} homln_subset_result;
+
+/* Every subset of at least `min_layers` layers (Section 1: any r <= l layers; Section 6.1: the
+ * layers are analysed once and reused for every subset). All layers and every subset's AND
+ * graph are analysed in one persistent launch (results cached), then for each subset the
+ * ground truth, the `heuristic` estimate and their accuracy are computed with `sel`.
+ * out (host, capacity entries) receives the subsets in increasing mask order; count_out (host)
+ * the number of subsets (2^l - 1 minus the smaller ones). Errors: EINVAL, ERANGE (capacity),
+ * ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_subset_sweep(homln_t h, int32_t heuristic, const homln_select *sel, int32_t min_layers,
+                                          homln_subset_result *out, int32_t capacity, int32_t *count_out);
+
 /* Accuracy of `pred` against `truth` (node-id lists, host or device, duplicates ignored),
  * over the handle's node set. Errors: EINVAL (negative length, id outside [0, n)), ENOMEM, ECUDA. */
 HOMLN_API homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, const int32_t *truth,

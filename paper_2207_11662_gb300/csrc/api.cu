@@ -581,6 +581,45 @@ homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, co
     API_END
 }
 
+homln_status homln_subset_sweep(homln_t h, int32_t heuristic, const homln_select *sel, int32_t min_layers,
+                                homln_subset_result *out, int32_t capacity, int32_t *count_out) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    check_select(sel);
+    if (!count_out) fail(HOMLN_EINVAL, "count_out is NULL");
+    if (heuristic < HOMLN_NAIVE || heuristic > HOMLN_CC2) fail(HOMLN_EINVAL, "unknown heuristic");
+    if (h->L > 20) fail(HOMLN_EINVAL, "a sweep covers at most 20 layers (2^20 subsets)");
+    use_device(h);
+    std::vector<uint64_t> masks;
+    for (uint64_t m = 1; m < (1ull << h->L); ++m)
+        if (__builtin_popcountll(m) >= std::max(1, min_layers)) masks.push_back(m);
+    *count_out = (int32_t)masks.size();
+    if (!out) { set_error(""); return HOMLN_OK; }
+    if (capacity < (int32_t)masks.size()) fail(HOMLN_ERANGE, "capacity smaller than the number of subsets");
+    // Psi once: every layer and every subset's AND graph, one launch
+    std::vector<GraphState *> gs;
+    for (auto &g : h->layers) gs.push_back(g.get());
+    for (uint64_t m : masks) gs.push_back(&and_graph(h, m));
+    analyse_many(h, gs);
+    const int32_t n = h->n;
+    DBuf<int32_t> est;
+    if (!est.alloc(&h->al, n)) fail(HOMLN_ENOMEM, "sweep scratch");
+    for (size_t i = 0; i < masks.size(); ++i) {
+        Selection &T = selection_of(h, and_graph(h, masks[i]), *sel);
+        int32_t c = 0;
+        homln_status st = homln_compose(h, masks[i], heuristic, sel, est.p, &c);
+        if (st != HOMLN_OK) fail(st, homln_last_error());
+        homln_accuracy_t acc;
+        accuracy_counts(n, est.p, c, T.ranked.p, T.count, &acc, h->err.p, &h->al, h->stream);
+        out[i].mask = masks[i];
+        out[i].truth_count = T.count;
+        out[i].estimate_count = c;
+        out[i].acc = acc;
+    }
+    check_device_error(h);
+    API_END
+}
+
 homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_pred, const int32_t *truth, int32_t n_truth,
                             homln_accuracy_t *out) {
     API_BEGIN

@@ -33,6 +33,7 @@ EXPORTS = [
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
+    "homln_subset_sweep",
 ]
 
 
@@ -47,6 +48,11 @@ class homln_accuracy_t(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class homln_subset_result(ctypes.Structure):
+    _fields_ = [("mask", c_uint64), ("truth_count", c_int32), ("estimate_count", c_int32),
+                ("acc", homln_accuracy_t)]
 
 
 class homln_tuning(ctypes.Structure):
@@ -104,6 +110,8 @@ def _load():
         "homln_kernel_launches": (c_int64, []),
         "homln_sync": (S, [c_void_p]),
         "homln_invalidate": (S, [c_void_p]),
+        "homln_subset_sweep": (S, [c_void_p, c_int32, POINTER(homln_select), c_int32, POINTER(homln_subset_result),
+                                   c_int32, POINTER(c_int32)]),
         "homln_last_error": (c_char_p, []),
         "homln_version": (c_char_p, []),
         "homln_accuracy_noalloc": (S, [c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
@@ -267,6 +275,17 @@ def homln_reset_profile(h) -> None:
 
 def homln_kernel_launches() -> int:
     return int(lib.homln_kernel_launches())
+
+
+def homln_subset_sweep(h, heuristic: int, sel, min_layers: int = 2) -> list:
+    cnt = c_int32()
+    _check(lib.homln_subset_sweep(h, int(heuristic), ctypes.byref(sel), int(min_layers), None, 0, ctypes.byref(cnt)),
+           "homln_subset_sweep")
+    out = (homln_subset_result * max(cnt.value, 1))()
+    _check(lib.homln_subset_sweep(h, int(heuristic), ctypes.byref(sel), int(min_layers), out, cnt.value,
+                                  ctypes.byref(cnt)), "homln_subset_sweep")
+    return [{"mask": r.mask, "truth_count": r.truth_count, "estimate_count": r.estimate_count, **r.acc.as_dict()}
+            for r in out[:cnt.value]]
 
 
 def homln_invalidate(h) -> None:

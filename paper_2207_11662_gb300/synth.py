@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "HoMLN", "er_edges", "chung_lu_edges", "ba_edges", "overlay",
     "homln_small_er", "homln_small_overlap", "homln_powerlaw", "homln_ba_large",
-    "homln_batch", "serving_requests", "noisy_copy", "relabel",
+    "homln_batch", "serving_requests", "noisy_copy", "relabel", "rmat_edges", "homln_parmat_like",
 ]
 
 
@@ -187,6 +187,45 @@ def noisy_copy(n: int, edges, seed: int, self_loops: int = 8, duplicates: int = 
 # ---------------------------------------------------------------------------
 # Workloads shaped like the paper's (Section 6) and the benchmark configurations
 # ---------------------------------------------------------------------------
+
+RMAT_POWERLAW = (0.45, 0.15, 0.15)  # a, b, c (d = 0.25): skewed, power-law degrees
+RMAT_NORMAL = (0.25, 0.25, 0.25)    # uniform quadrants: binomial (normal-like) degrees
+
+
+def rmat_edges(n: int, m: int, seed: int, abc=RMAT_POWERLAW):
+    """R-MAT: each edge picks one quadrant of the adjacency matrix per bit of the node id with
+    probabilities (a, b, c, d); ids >= n are folded back with a modulus. Repeats and self loops
+    are kept (the library normalises its input)."""
+    a, b, c = abc
+    rng = _rng(seed)
+    scale = max(1, int(math.ceil(math.log2(max(n, 2)))))
+    u = np.zeros(m, np.int64)
+    v = np.zeros(m, np.int64)
+    for _ in range(scale):
+        r = rng.random(m)
+        ubit = r >= a + b
+        vbit = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+        u = (u << 1) | ubit
+        v = (v << 1) | vbit
+    perm = rng.permutation(n)  # random node labels, so high-degree nodes are not the small ids
+    return perm[u % n].astype(np.int32), perm[v % n].astype(np.int32)
+
+
+def homln_parmat_like(n: int = 50000, m: int = 250000, split=(0.7, 0.3), kinds=("powerlaw", "normal"),
+                      seed: int = 6001) -> HoMLN:
+    """A two-layer HoMLN shaped like the paper's synthetic sets (Section 6, Table 1): layer i holds
+    split[i] of the base graph's m edges from its own R-MAT generator (power-law or normal) plus
+    a shared backbone of n edges (a random Hamiltonian cycle), which Table 1's counts imply
+    (|L_i| ~ split_i * m + |V|, |L1 AND L2| ~ |V|)."""
+    rng = _rng(seed)
+    order = rng.permutation(n)
+    backbone = (order.astype(np.int32), np.roll(order, 1).astype(np.int32))
+    layers = []
+    for i, (frac, kind) in enumerate(zip(split, kinds)):
+        own = rmat_edges(n, int(round(frac * m)), seed * 10 + i, RMAT_POWERLAW if kind == "powerlaw" else RMAT_NORMAL)
+        layers.append((np.concatenate([backbone[0], own[0]]), np.concatenate([backbone[1], own[1]])))
+    return HoMLN(n, layers, name=f"parmat{n}-{m}-{split[0]:.1f}", meta={"kinds": kinds, "split": split})
+
 
 def homln_small_er(n: int = 1000, avg_deg: float = 8.0, n_layers: int = 3, seeds=(101, 102, 103)) -> HoMLN:
     """Independent ER layers on a shared node set (3 x ER(1000, m=4000))."""

@@ -162,6 +162,25 @@ def test_batch_analyse_across_handles(H):
         g.close()
 
 
+def test_subset_sweep(H):
+    """Every subset of at least two of four layers: ground truth, estimate and accuracy vs the oracle."""
+    net = synth.homln_small_overlap(900, 9.0, 4, 0.5, 61)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    g = H.Network(net.n, to_dev(net.layers))
+    for heur in (H.HOMLN_NAIVE, H.HOMLN_CC1, H.HOMLN_CC2):
+        sel, osel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)
+        res = H.homln_subset_sweep(g.h, heur, sel, 2)
+        assert [r["mask"] for r in res] == [m for m in range(1, 16) if bin(m).count("1") >= 2]
+        for r in res:
+            gt = ref.topk(-1, r["mask"], osel)
+            est = ref.compose(r["mask"], heur, osel)
+            want = O.accuracy(est, gt)
+            assert (r["truth_count"], r["estimate_count"]) == (len(gt), len(est))
+            assert (r["tp"], r["fp"], r["fn"]) == (want["tp"], want["fp"], want["fn"])
+            assert r["jaccard"] == pytest.approx(want["jaccard"], rel=REL_TOL, abs=0)
+    g.close()
+
+
 def test_hubs_use_block_and_warp_tiers(H):
     """A star plus a power-law layer: the centre's row exceeds the block threshold."""
     n = 5000
