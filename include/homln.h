@@ -189,8 +189,18 @@ HOMLN_API homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64
  * Same outputs and rules as homln_layer_closeness. */
 HOMLN_API homln_status homln_and_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach, double *cc);
 
-/* CC nodes of one graph: which = layer id, or -1 for the AND graph of layer_mask (then the
- * ground truth). Scores are the closeness values of homln_*_closeness; the selection rule
+/* Boolean OR aggregation (Section 3.1 names it as the alternative to AND): an edge is kept iff
+ * it is present in at least one selected layer. Built once per mask and cached; same output
+ * conventions and errors as homln_and_aggregate. */
+HOMLN_API homln_status homln_or_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity, int32_t *or_src,
+                                          int32_t *or_dst, int64_t *or_edge_count);
+
+/* All-sources BFS closeness of the OR graph of `layer_mask`; same outputs as homln_layer_closeness. */
+HOMLN_API homln_status homln_or_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach,
+                                          double *cc);
+
+/* CC nodes of one graph: which = layer id, -1 for the AND graph of layer_mask (the ground
+ * truth), or -2 for the OR graph of layer_mask. Scores are the closeness values of homln_*_closeness; the selection rule
  * is `sel`. nodes_out (capacity n, host or device) receives the ids in rank order;
  * count_out (host) the number written.
  * Errors: EINVAL (which/mask/sel), ENOMEM, ECUDA, ETIMEOUT. */

@@ -126,6 +126,14 @@ def and_keys(n: int, layer_keys) -> np.ndarray:
     return out
 
 
+def or_keys(n: int, layer_keys) -> np.ndarray:
+    """Edges present in at least one given layer (Boolean OR aggregation, Section 3.1)."""
+    out = layer_keys[0]
+    for k in layer_keys[1:]:
+        out = np.union1d(out, k)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Distances (Section 4: BFS from every vertex, unreachable contributes 0)
 # ---------------------------------------------------------------------------
@@ -358,6 +366,7 @@ class OracleHoMLN:
         self.keys = [edge_keys(n, s, d) for s, d in layers]
         self._layer = {}
         self._and = {}
+        self._or = {}
 
     def _analyse(self, keys):
         n = self.n
@@ -380,11 +389,20 @@ class OracleHoMLN:
             self._and[mask] = self._analyse(and_keys(self.n, [self.keys[i] for i in ids]))
         return self._and[mask]
 
+    def or_graph(self, mask: int) -> dict:
+        if mask not in self._or:
+            ids = self.mask_layers(mask)
+            self._or[mask] = self._analyse(or_keys(self.n, [self.keys[i] for i in ids]))
+        return self._or[mask]
+
+    def or_edges(self, mask: int):
+        return keys_to_edges(self.n, self.or_graph(mask)["keys"])
+
     def and_edges(self, mask: int):
         return keys_to_edges(self.n, self.and_graph(mask)["keys"])
 
     def topk(self, which: int, mask: int, sel: Select) -> np.ndarray:
-        g = self.and_graph(mask) if which < 0 else self.layer(which)
+        g = self.layer(which) if which >= 0 else self.and_graph(mask) if which == -1 else self.or_graph(mask)
         return select(g["cc"], sel)
 
     def compose(self, mask: int, heur: int, sel: Select) -> np.ndarray:

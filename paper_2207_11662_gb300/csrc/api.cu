@@ -83,6 +83,7 @@ struct homln_s {
     DBuf<int32_t> err;
     std::vector<std::unique_ptr<GraphState>> layers;
     std::map<uint64_t, std::unique_ptr<GraphState>> ands;
+    std::map<uint64_t, std::unique_ptr<GraphState>> ors;
     bool profiling = false;
     bool instrument = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -320,6 +321,19 @@ Selection &selection_of(homln_t h, GraphState &g, const homln_select &sel) {
     return ref;
 }
 
+GraphState &or_graph(homln_t h, uint64_t mask) {
+    std::vector<int> ids = mask_layers(h, mask);
+    auto it = h->ors.find(mask);
+    if (it != h->ors.end()) return *it->second;
+    auto g = std::make_unique<GraphState>();
+    std::vector<const Csr *> ls;
+    for (int i : ids) ls.push_back(&h->layers[i]->csr);
+    or_union(h->n, ls, g->csr, &h->al, h->stream);
+    GraphState &ref = *g;
+    h->ors.emplace(mask, std::move(g));
+    return ref;
+}
+
 void check_select(const homln_select *sel) {
     if (!sel) fail(HOMLN_EINVAL, "selection is NULL");
     if (sel->reserved != 0) fail(HOMLN_EINVAL, "homln_select.reserved must be 0");
@@ -496,6 +510,42 @@ homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64_t capacit
     API_END
 }
 
+homln_status homln_or_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity, int32_t *or_src, int32_t *or_dst,
+                                int64_t *or_edge_count) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!or_edge_count) fail(HOMLN_EINVAL, "or_edge_count is NULL");
+    if ((or_src == nullptr) != (or_dst == nullptr)) fail(HOMLN_EINVAL, "or_src and or_dst must both be given");
+    use_device(h);
+    GraphState &g = or_graph(h, layer_mask);
+    const int64_t m = g.csr.nnz / 2;
+    if (or_src) {
+        if (capacity < m) {
+            *or_edge_count = m;
+            fail(HOMLN_ERANGE, "capacity smaller than the OR edge count");
+        }
+        DevOut<int32_t> os, od;
+        os.to(h, or_src, m);
+        od.to(h, or_dst, m);
+        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream);
+        bool host = os.finish(h, m);
+        host |= od.finish(h, m);
+        if (host) HCUDA(cudaStreamSynchronize(h->stream));
+    }
+    *or_edge_count = m;
+    API_END
+}
+
+homln_status homln_or_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach, double *cc) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    use_device(h);
+    GraphState &g = or_graph(h, layer_mask);
+    analyse(h, g);
+    write_closeness(h, g, farness, reach, cc);
+    API_END
+}
+
 homln_status homln_and_closeness(homln_t h, uint64_t layer_mask, uint64_t *farness, uint32_t *reach, double *cc) {
     API_BEGIN
     if (!h) fail(HOMLN_EINVAL, "null handle");
@@ -512,9 +562,9 @@ homln_status homln_topk(homln_t h, int32_t which, uint64_t layer_mask, const hom
     if (!h) fail(HOMLN_EINVAL, "null handle");
     check_select(sel);
     if (!count_out) fail(HOMLN_EINVAL, "count_out is NULL");
-    if (which < -1 || which >= h->L) fail(HOMLN_EINVAL, "which must be -1 or a layer id");
+    if (which < -2 || which >= h->L) fail(HOMLN_EINVAL, "which must be -2, -1 or a layer id");
     use_device(h);
-    GraphState &g = which >= 0 ? *h->layers[which] : and_graph(h, layer_mask);
+    GraphState &g = which >= 0 ? *h->layers[which] : which == -1 ? and_graph(h, layer_mask) : or_graph(h, layer_mask);
     analyse(h, g);
     Selection &S = selection_of(h, g, *sel);
     const int32_t c = S.count;
@@ -653,6 +703,7 @@ homln_status homln_invalidate(homln_t h) {
     };
     for (auto &g : h->layers) drop(*g);
     for (auto &kv : h->ands) drop(*kv.second);
+    for (auto &kv : h->ors) drop(*kv.second);
     API_END
 }
 

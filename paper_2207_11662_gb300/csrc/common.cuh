@@ -194,6 +194,8 @@ void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
                Alloc *al, cudaStream_t s);
 // Edges present in every CSR of `layers` (sorted-row intersection).
 void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s);
+// Edges present in at least one CSR of `layers` (Boolean OR aggregation).
+void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s);
 // Undirected edge list u < v, ascending (u, v), of a CSR. Writes nnz/2 pairs.
 void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s);
 // Degree-descending relabelling: perm[new] = old; builds the relabelled CSR.

@@ -133,6 +133,29 @@ __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, con
     }
 }
 
+// Row u of the concatenation: every selected layer's row u, one after the other.
+__global__ void k_sum_degrees(int32_t n, LayerSet L, int32_t *__restrict__ deg) {
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int64_t d = 0;
+        for (int i = 0; i < L.r; ++i) d += L.rp[i][u + 1] - L.rp[i][u];
+        deg[u] = (int32_t)d;
+    }
+}
+
+__global__ void k_concat_rows(int32_t n, LayerSet L, const int64_t *__restrict__ orp, int32_t *__restrict__ ocol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        int64_t o = orp[u];
+        for (int i = 0; i < L.r; ++i) {
+            const int64_t b = L.rp[i][u], len = L.rp[i][u + 1] - b;
+            for (int64_t j = lane; j < len; j += 32) ocol[o + j] = L.col[i][b + j];
+            o += len;
+        }
+    }
+}
+
 // Length of the part of row u holding neighbours v > u (rows are sorted).
 __global__ void k_upper_len(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                             int32_t *__restrict__ len, int64_t *__restrict__ start) {
@@ -242,6 +265,35 @@ void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, 
     if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "and col");
     if (out.nnz > 0)
         launch(k_and_rows<true>, grid_for((int64_t)n * 32), 256, 0, s, n, L, nullptr, out.rowptr.p, out.col.p);
+    HCUDA(cudaGetLastError());
+}
+
+void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s) {
+    LayerSet L{};
+    L.r = (int)layers.size();
+    for (int i = 0; i < L.r; ++i) {
+        L.rp[i] = layers[i]->rowptr.p;
+        L.col[i] = layers[i]->col.p;
+    }
+    out.n = n;
+    DBuf<int32_t> deg, cat, cnt;
+    DBuf<int64_t> rp;
+    if (!out.rowptr.alloc(al, (size_t)n + 1) || !deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cnt.alloc(al, n))
+        fail(HOMLN_ENOMEM, "or scratch");
+    launch(k_sum_degrees, grid_for(n), 256, 0, s, n, L, deg.p);
+    scan_exclusive_i32(deg.p, rp.p, n, al, s);
+    const int64_t total = read_i64(rp.p + n, s);
+    if (!cat.alloc(al, total > 0 ? total : 1)) fail(HOMLN_ENOMEM, "or rows");
+    launch(k_concat_rows, grid_for((int64_t)n * 32), 256, 0, s, n, L, (const int64_t *)rp.p, cat.p);
+    sort_rows(n, rp.p, cat.p, al, s);
+    launch(k_row_unique<false>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
+           (const int32_t *)cat.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr);
+    scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
+    out.nnz = read_i64(out.rowptr.p + n, s);
+    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "or col");
+    if (out.nnz > 0)
+        launch(k_row_unique<true>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
+               (const int32_t *)cat.p, (int32_t *)nullptr, (const int64_t *)out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
 }
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
-    "homln_subset_sweep",
+    "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness",
 ]
 
 
@@ -101,6 +101,8 @@ def _load():
         "homln_batch_analyse": (S, [POINTER(c_void_p), c_int32, POINTER(c_uint64), c_int32]),
         "homln_and_aggregate": (S, [c_void_p, c_uint64, c_int64, c_void_p, c_void_p, POINTER(c_int64)]),
         "homln_and_closeness": (S, [c_void_p, c_uint64, c_void_p, c_void_p, c_void_p]),
+        "homln_or_aggregate": (S, [c_void_p, c_uint64, c_int64, c_void_p, c_void_p, POINTER(c_int64)]),
+        "homln_or_closeness": (S, [c_void_p, c_uint64, c_void_p, c_void_p, c_void_p]),
         "homln_topk": (S, [c_void_p, c_int32, c_uint64, POINTER(homln_select), c_void_p, POINTER(c_int32)]),
         "homln_compose": (S, [c_void_p, c_uint64, c_int32, POINTER(homln_select), c_void_p, POINTER(c_int32)]),
         "homln_accuracy": (S, [c_void_p, c_void_p, c_int32, c_void_p, c_int32, POINTER(homln_accuracy_t)]),
@@ -229,6 +231,17 @@ def homln_and_closeness(h, layer_mask: int, farness=None, reach=None, cc=None) -
     _check(lib.homln_and_closeness(h, int(layer_mask), ptr(farness), ptr(reach), ptr(cc)), "homln_and_closeness")
 
 
+def homln_or_aggregate(h, layer_mask: int, capacity: int = 0, or_src=None, or_dst=None) -> int:
+    cnt = c_int64()
+    _check(lib.homln_or_aggregate(h, int(layer_mask), int(capacity), ptr(or_src), ptr(or_dst), ctypes.byref(cnt)),
+           "homln_or_aggregate")
+    return cnt.value
+
+
+def homln_or_closeness(h, layer_mask: int, farness=None, reach=None, cc=None) -> None:
+    _check(lib.homln_or_closeness(h, int(layer_mask), ptr(farness), ptr(reach), ptr(cc)), "homln_or_closeness")
+
+
 def homln_topk(h, which: int, layer_mask: int, sel, nodes_out) -> int:
     cnt = c_int32()
     _check(lib.homln_topk(h, int(which), int(layer_mask), ctypes.byref(sel), ptr(nodes_out), ctypes.byref(cnt)),
@@ -339,6 +352,18 @@ class Network:
             self._empty(self.n, self.torch.float64)
         homln_and_closeness(self.h, mask, F, R, cc)
         return F[:self.n], R[:self.n], cc[:self.n]
+
+    def or_closeness(self, mask: int):
+        F, R, cc = self._empty(self.n, self.torch.int64), self._empty(self.n, self.torch.int32), \
+            self._empty(self.n, self.torch.float64)
+        homln_or_closeness(self.h, mask, F, R, cc)
+        return F[:self.n], R[:self.n], cc[:self.n]
+
+    def or_aggregate(self, mask: int):
+        m = homln_or_aggregate(self.h, mask)
+        s, d = self._empty(m, self.torch.int32), self._empty(m, self.torch.int32)
+        homln_or_aggregate(self.h, mask, m, s, d)
+        return s[:m], d[:m]
 
     def and_aggregate(self, mask: int):
         m = homln_and_aggregate(self.h, mask)

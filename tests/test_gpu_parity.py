@@ -181,6 +181,22 @@ def test_subset_sweep(H):
     g.close()
 
 
+def test_or_aggregation(H):
+    """OR graphs (edges in at least one selected layer): edge lists, closeness and top-k vs the oracle."""
+    net = synth.homln_small_overlap(1200, 6.0, 3, 0.3, 71)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    g = H.Network(net.n, to_dev(net.layers))
+    sel, osel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)
+    for mask in (7, 5, 2):
+        s, d = g.or_aggregate(mask)
+        rs, rd = ref.or_edges(mask)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(d.cpu().numpy(), rd)
+        check_graph(*g.or_closeness(mask), ref.or_graph(mask))
+        out = g.topk(-2, mask, sel)
+        assert out.cpu().numpy().tolist() == ref.topk(-2, mask, osel).tolist()
+    g.close()
+
+
 def test_hubs_use_block_and_warp_tiers(H):
     """A star plus a power-law layer: the centre's row exceeds the block threshold."""
     n = 5000

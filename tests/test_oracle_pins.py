@@ -195,6 +195,13 @@ def test_and_aggregation_invariants():
     assert np.array_equal(O.and_keys(n, [keys[1], keys[1]]), keys[1])  # identical layers
     assert O.and_keys(n, [keys[0], np.zeros(0, np.int64)]).size == 0  # with an empty layer
     assert a.size > 0
+    # OR aggregation: brute-force union; every layer is a subset of it; AND is a subset of OR
+    o = O.or_keys(n, keys)
+    union = set()
+    for s, d in net.layers:
+        union |= brute_edge_set(zip(s.tolist(), d.tolist()))
+    assert [tuple(map(int, x)) for x in zip(*O.keys_to_edges(n, o))] == sorted(union)
+    assert all(np.all(np.isin(k, o)) for k in keys) and np.all(np.isin(a, o))
 
 
 # ---------------------------------------------------------------- selection
