@@ -97,6 +97,27 @@ def edge_keys(n: int, src, dst) -> np.ndarray:
     return np.unique(lo * n + hi)
 
 
+def arc_keys(n: int, src, dst) -> np.ndarray:
+    """A directed layer's arc set as sorted unique keys u*n+v for arcs u -> v (self loops and repeats dropped)."""
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    if s.size and (s.min() < 0 or d.min() < 0 or s.max() >= n or d.max() >= n):
+        raise ValueError("node id out of range")
+    keep = s != d
+    return np.unique(s[keep] * n + d[keep])
+
+
+def arc_csr(n: int, keys: np.ndarray, reverse: bool = False):
+    """CSR of arcs: rows are tails (out-edges), or heads with reverse=True (in-edges); rows sorted."""
+    u, v = (np.asarray(keys, np.int64) // n, np.asarray(keys, np.int64) % n)
+    rows, cols = (v, u) if reverse else (u, v)
+    order = np.lexsort((cols, rows))
+    rows, cols = rows[order], cols[order]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    return rowptr, cols.astype(np.int32)
+
+
 def keys_to_edges(n: int, keys: np.ndarray):
     keys = np.asarray(keys, np.int64)
     return (keys // n).astype(np.int32), (keys % n).astype(np.int32)
@@ -360,17 +381,22 @@ def accuracy(pred, truth) -> dict:
 # ---------------------------------------------------------------------------
 
 class OracleHoMLN:
-    def __init__(self, n: int, layers, threads: int = 1):
+    """directed=True: layers are arc lists; closeness is in-closeness (distances d(v, u) of the
+    vertices v that reach u, the NetworkX convention for directed graphs), i.e. BFS from u along
+    in-edges; degrees are in-degrees and CC1's neighbourhoods are in-neighbourhoods."""
+
+    def __init__(self, n: int, layers, threads: int = 1, directed: bool = False):
         self.n = int(n)
         self.threads = threads
-        self.keys = [edge_keys(n, s, d) for s, d in layers]
+        self.directed = directed
+        self.keys = [arc_keys(n, s, d) if directed else edge_keys(n, s, d) for s, d in layers]
         self._layer = {}
         self._and = {}
         self._or = {}
 
     def _analyse(self, keys):
         n = self.n
-        rowptr, col = csr_from_keys(n, keys)
+        rowptr, col = arc_csr(n, keys, reverse=True) if self.directed else csr_from_keys(n, keys)
         F, R = farness_reach(n, rowptr, col, threads=self.threads)
         return {"rowptr": rowptr, "col": col, "F": F, "R": R, "cc": wf_closeness(n, F, R),
                 "sumdist": sum_dist_n(n, F, R), "deg": degrees(rowptr), "keys": keys}

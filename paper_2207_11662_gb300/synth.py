@@ -192,6 +192,13 @@ RMAT_POWERLAW = (0.45, 0.15, 0.15)  # a, b, c (d = 0.25): skewed, power-law degr
 RMAT_NORMAL = (0.25, 0.25, 0.25)    # uniform quadrants: binomial (normal-like) degrees
 
 
+def with_reciprocal(edges, frac: float, seed: int):
+    """Arc list plus the reverse of a random ``frac`` of its arcs (directed layers with some 2-cycles)."""
+    s, d = edges
+    pick = _rng(seed).random(s.shape[0]) < frac
+    return np.concatenate([s, d[pick]]).astype(np.int32), np.concatenate([d, s[pick]]).astype(np.int32)
+
+
 def rmat_edges(n: int, m: int, seed: int, abc=RMAT_POWERLAW):
     """R-MAT: each edge picks one quadrant of the adjacency matrix per bit of the node id with
     probabilities (a, b, c, d); ids >= n are folded back with a modulus. Repeats and self loops

@@ -347,3 +347,68 @@ def test_accuracy_metrics():
     assert (e["jaccard"], e["precision"], e["recall"], e["f1"]) == (1.0, 0.0, 0.0, 0.0)
     z = O.accuracy([1], [2])
     assert (z["tp"], z["fp"], z["fn"], z["jaccard"], z["f1"]) == (0, 1, 1, 0.0, 0.0)
+
+
+# ---------------------------------------------------------------- directed layers (Section 4: closeness
+# is defined for directed graphs too; in-closeness, the NetworkX convention)
+
+def directed_fr(n, pairs):
+    net = O.OracleHoMLN(n, [edges_of(pairs)], directed=True)
+    L = net.layer(0)
+    return L["F"], L["R"], L["deg"]
+
+
+def test_directed_path_and_cycle_closed_forms():
+    n = 12
+    F, R, deg = directed_fr(n, [(i, i + 1) for i in range(n - 1)])  # 0 -> 1 -> ... -> n-1
+    for i in range(n):
+        assert F[i] == i * (i + 1) // 2 and R[i] == i  # reached from 0..i-1 at distances i..1
+        assert deg[i] == (1 if i > 0 else 0)  # in-degree
+    F, R, _ = directed_fr(n, [(i, (i + 1) % n) for i in range(n)])
+    assert np.all(F == n * (n - 1) // 2) and np.all(R == n - 1)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_directed_floyd_warshall(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 30))
+    pairs = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(int(rng.integers(1, 3 * n)))]
+    D = np.full((n, n), np.inf)
+    np.fill_diagonal(D, 0)
+    for a, b in pairs:
+        if a != b:
+            D[a, b] = 1
+    for k in range(n):
+        D = np.minimum(D, D[:, [k]] + D[[k], :])
+    F, R, _ = directed_fr(n, pairs)
+    fin = np.isfinite(D)
+    # in-closeness of u: distances d(v, u) over the v that reach u (column u)
+    assert np.array_equal(F, np.where(fin, D, 0).sum(axis=0).astype(np.uint64))
+    assert np.array_equal(R, (fin.sum(axis=0) - 1).astype(np.uint32))
+
+
+def test_directed_symmetric_arcs_reduce_to_undirected():
+    """Every arc together with its reverse: in-closeness equals undirected closeness."""
+    net = synth.homln_small_overlap(300, 5.0, 2, 0.4, 17)
+    und = O.OracleHoMLN(net.n, net.layers)
+    both = [(np.concatenate([s, d]), np.concatenate([d, s])) for s, d in net.layers]
+    dire = O.OracleHoMLN(net.n, both, directed=True)
+    for i in range(2):
+        for k in ("F", "R", "cc", "deg"):
+            assert np.array_equal(dire.layer(i)[k], und.layer(i)[k]), k
+    for k in ("F", "R", "cc"):
+        assert np.array_equal(dire.and_graph(3)[k], und.and_graph(3)[k])
+        assert np.array_equal(dire.or_graph(3)[k], und.or_graph(3)[k])
+
+
+def test_directed_aggregates_are_arc_sets():
+    """An arc and its reverse are different arcs: AND keeps only arcs present with the same direction."""
+    n = 4
+    x = edges_of([(0, 1), (1, 2), (2, 3)])
+    y = edges_of([(1, 0), (1, 2), (3, 2)])
+    net = O.OracleHoMLN(n, [x, y], directed=True)
+    s, d = net.and_edges(3)
+    assert list(zip(s.tolist(), d.tolist())) == [(1, 2)]
+    s, d = net.or_edges(3)
+    assert list(zip(s.tolist(), d.tolist())) == [(0, 1), (1, 0), (1, 2), (2, 3), (3, 2)]
+    assert net.and_graph(3)["deg"].tolist() == [0, 0, 1, 0]  # in-degrees
