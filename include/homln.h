@@ -62,8 +62,13 @@ typedef enum homln_status {
 } homln_status;
 
 /* homln_create flags */
-#define HOMLN_PTR_HOST 0u   /* edge arrays are host memory */
+#define HOMLN_PTR_HOST 0u   /* edge arrays are host memory (flags are a bitwise OR) */
 #define HOMLN_PTR_DEVICE 1u /* edge arrays are device memory of the current device */
+#define HOMLN_DIRECTED 2u   /* layers are directed: (src, dst) is an arc src -> dst (Section 4 defines
+                               closeness for directed graphs too). Closeness is then in-closeness, from
+                               the distances d(v, u) of the vertices v that reach u (as NetworkX computes
+                               it for directed graphs); reach counts those v; degrees are in-degrees
+                               and CC1's one-hop neighbours are in-neighbours; edge lists are arcs. */
 
 /* Composition heuristics: naive (Section 4), CC1 (Section 5.1), CC2 (Section 5.2, Algorithm 1). */
 typedef enum homln_heuristic { HOMLN_NAIVE = 0, HOMLN_CC1 = 1, HOMLN_CC2 = 2 } homln_heuristic;

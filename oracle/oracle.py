@@ -15,7 +15,7 @@ to be read against the paper:
 * Wasserman-Faust normalised closeness, which reduces to Eq. 1 on a connected
   graph (Section 4),
 * sumDist with the "unreachable costs n" convention (Section 5.1),
-* CC-node selection: top-k, or "same or above average" (Section 4, Section 5.2),
+* CC-node selection: top-k, or at or above the average (Section 4, Section 5.2),
 * composition heuristics naive (Section 4), CC1 (Section 5.1, Eqs. 2-3) and
   CC2 (Section 5.2, Algorithm 1),
 * Jaccard / precision / recall / F1 of an estimated set against ground truth
@@ -23,7 +23,7 @@ to be read against the paper:
 
 Floating point: closeness values are float64, as in the paper's NetworkX runs.
 Each is one correctly rounded division of exact integers. Decisions that
-depend on an average ("same or above average") are taken exactly on those
+depend on an average (at or above the average) are taken exactly on those
 float64 values with ``fractions.Fraction`` (no summation-order dependence).
 
 Parity status: everything is pinned by tests in ``tests/test_oracle_*.py``
@@ -226,7 +226,7 @@ def degrees(rowptr) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# CC-node selection (top-k, or "same or above average")
+# CC-node selection (top-k, or at or above the average)
 # ---------------------------------------------------------------------------
 
 @dataclass

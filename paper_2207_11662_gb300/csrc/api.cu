@@ -58,7 +58,8 @@ struct Selection {
 
 // Partial results of one analysed graph (a layer or an AND aggregate).
 struct GraphState {
-    Csr csr;
+    Csr csr;     // rows = out-edges (all edges if undirected)
+    Csr csr_in;  // rows = in-edges; directed graphs only
     bool analysed = false;
     DBuf<uint64_t> F;
     DBuf<uint32_t> R;
@@ -79,6 +80,7 @@ struct homln_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     int32_t n = 0, L = 0;
+    bool directed = false;
     BfsTuning tuning;
     DBuf<int32_t> err;
     std::vector<std::unique_ptr<GraphState>> layers;
@@ -128,6 +130,11 @@ bool is_device_ptr(const void *p) {
 }
 
 void use_device(homln_t h) { HCUDA(cudaSetDevice(h->device)); }
+
+// The CSR whose rows are the neighbours that reach a vertex: the in-edges of a directed graph.
+const Csr &in_csr(homln_t h, const GraphState &g) { return h->directed ? g.csr_in : g.csr; }
+
+int64_t edge_count(homln_t h, const GraphState &g) { return h->directed ? g.csr.nnz : g.csr.nnz / 2; }
 
 // Map a device-side error word to a status (and clear it).
 void check_device_error(homln_t h) {
@@ -212,7 +219,7 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
             !g->sumdist.alloc(&o->al, n) || !g->deg.alloc(&o->al, n))
             fail(HOMLN_ENOMEM, "closeness outputs");
         if (!g->bfs_ready || g->bfs.relabeled != (h->tuning.relabel != 0)) {
-            bfs_prepare(g->csr, h->tuning.relabel != 0, g->bfs, &o->al, o->stream);
+            bfs_prepare(g->csr, o->directed ? &g->csr_in : nullptr, h->tuning.relabel != 0, g->bfs, &o->al, o->stream);
             g->bfs_ready = true;
         }
         jobs.push_back(BfsJob{&g->bfs, g->F.p, g->R.p});
@@ -251,7 +258,8 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
     h->bfs_launches += 1;
     for (const auto &it : todo) {
         GraphState *g = it.second;
-        closeness_finalize(it.first->n, g->csr.rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p, g->deg.p, h->stream);
+        closeness_finalize(it.first->n, in_csr(it.first, *g).rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p, g->deg.p,
+                           h->stream);
         g->analysed = true;
     }
     for (homln_t o : others) {  // and the other streams wait for the results
@@ -285,21 +293,28 @@ GraphState &and_graph(homln_t h, uint64_t mask) {
     auto it = h->ands.find(mask);
     if (it != h->ands.end()) return *it->second;
     auto g = std::make_unique<GraphState>();
-    if (ids.size() == 1) {
-        const Csr &src = h->layers[ids[0]]->csr;
-        g->csr.n = src.n;
-        g->csr.nnz = src.nnz;
-        if (!g->csr.rowptr.alloc(&h->al, (size_t)h->n + 1) || !g->csr.col.alloc(&h->al, src.nnz > 0 ? src.nnz : 1))
+    auto copy = [&](const Csr &src, Csr &dst) {
+        dst.n = src.n;
+        dst.nnz = src.nnz;
+        if (!dst.rowptr.alloc(&h->al, (size_t)h->n + 1) || !dst.col.alloc(&h->al, src.nnz > 0 ? src.nnz : 1))
             fail(HOMLN_ENOMEM, "and graph");
-        HCUDA(cudaMemcpyAsync(g->csr.rowptr.p, src.rowptr.p, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToDevice,
+        HCUDA(cudaMemcpyAsync(dst.rowptr.p, src.rowptr.p, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToDevice,
                               h->stream));
         if (src.nnz > 0)
-            HCUDA(cudaMemcpyAsync(g->csr.col.p, src.col.p, sizeof(int32_t) * src.nnz, cudaMemcpyDeviceToDevice,
+            HCUDA(cudaMemcpyAsync(dst.col.p, src.col.p, sizeof(int32_t) * src.nnz, cudaMemcpyDeviceToDevice,
                                   h->stream));
+    };
+    if (ids.size() == 1) {
+        copy(h->layers[ids[0]]->csr, g->csr);
+        if (h->directed) copy(h->layers[ids[0]]->csr_in, g->csr_in);
     } else {
-        std::vector<const Csr *> ls;
-        for (int i : ids) ls.push_back(&h->layers[i]->csr);
+        std::vector<const Csr *> ls, lin;
+        for (int i : ids) {
+            ls.push_back(&h->layers[i]->csr);
+            lin.push_back(&h->layers[i]->csr_in);
+        }
         and_intersect(h->n, ls, g->csr, &h->al, h->stream);
+        if (h->directed) and_intersect(h->n, lin, g->csr_in, &h->al, h->stream);
     }
     GraphState &ref = *g;
     h->ands.emplace(mask, std::move(g));
@@ -326,9 +341,13 @@ GraphState &or_graph(homln_t h, uint64_t mask) {
     auto it = h->ors.find(mask);
     if (it != h->ors.end()) return *it->second;
     auto g = std::make_unique<GraphState>();
-    std::vector<const Csr *> ls;
-    for (int i : ids) ls.push_back(&h->layers[i]->csr);
+    std::vector<const Csr *> ls, lin;
+    for (int i : ids) {
+        ls.push_back(&h->layers[i]->csr);
+        lin.push_back(&h->layers[i]->csr_in);
+    }
     or_union(h->n, ls, g->csr, &h->al, h->stream);
+    if (h->directed) or_union(h->n, lin, g->csr_in, &h->al, h->stream);
     GraphState &ref = *g;
     h->ors.emplace(mask, std::move(g));
     return ref;
@@ -368,7 +387,7 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
     if (n_nodes < 1 || n_nodes > HOMLN_MAX_NODES) fail(HOMLN_EINVAL, "n_nodes must be in [1, 2^20]");
     if (n_layers < 1 || n_layers > HOMLN_MAX_LAYERS) fail(HOMLN_EINVAL, "n_layers must be in [1, 64]");
     if (!edge_counts || !src || !dst) fail(HOMLN_EINVAL, "edge_counts, src and dst must not be NULL");
-    if (flags > HOMLN_PTR_DEVICE) fail(HOMLN_EINVAL, "unknown flags");
+    if (flags & ~(HOMLN_PTR_DEVICE | HOMLN_DIRECTED)) fail(HOMLN_EINVAL, "unknown flags");
     for (int i = 0; i < n_layers; ++i) {
         if (edge_counts[i] < 0 || edge_counts[i] > (int64_t(1) << 31)) fail(HOMLN_EINVAL, "edge count out of range");
         if (edge_counts[i] > 0 && (!src[i] || !dst[i])) fail(HOMLN_EINVAL, "edge array is NULL");
@@ -382,6 +401,7 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
     else std::memset(&h->al.a, 0, sizeof(h->al.a));
     h->n = n_nodes;
     h->L = n_layers;
+    h->directed = (flags & HOMLN_DIRECTED) != 0;
     if (!h->err.alloc(&h->al, 1)) fail(HOMLN_ENOMEM, "error word");
     HCUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->stream));
     for (int i = 0; i < n_layers; ++i) {
@@ -389,14 +409,15 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
         const int64_t m = edge_counts[i];
         DBuf<int32_t> ds, dd;
         const int32_t *ps = src[i], *pd = dst[i];
-        if (m > 0 && flags == HOMLN_PTR_HOST) {
+        if (m > 0 && !(flags & HOMLN_PTR_DEVICE)) {
             if (!ds.alloc(&h->al, m) || !dd.alloc(&h->al, m)) fail(HOMLN_ENOMEM, "edge staging");
             HCUDA(cudaMemcpyAsync(ds.p, ps, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
             HCUDA(cudaMemcpyAsync(dd.p, pd, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
             ps = ds.p;
             pd = dd.p;
         }
-        build_csr(n_nodes, ps, pd, m, g->csr, h->err.p, &h->al, h->stream);
+        build_csr(n_nodes, ps, pd, m, g->csr, h->err.p, &h->al, h->stream, h->directed);
+        if (h->directed) build_csr(n_nodes, pd, ps, m, g->csr_in, h->err.p, &h->al, h->stream, true);
         h->layers.push_back(std::move(g));
     }
     check_device_error(h.get());
@@ -492,7 +513,7 @@ homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64_t capacit
     if ((and_src == nullptr) != (and_dst == nullptr)) fail(HOMLN_EINVAL, "and_src and and_dst must both be given");
     use_device(h);
     GraphState &g = and_graph(h, layer_mask);
-    const int64_t m = g.csr.nnz / 2;
+    const int64_t m = edge_count(h, g);
     if (and_src) {
         if (capacity < m) {
             *and_edge_count = m;
@@ -501,7 +522,7 @@ homln_status homln_and_aggregate(homln_t h, uint64_t layer_mask, int64_t capacit
         DevOut<int32_t> os, od;
         os.to(h, and_src, m);
         od.to(h, and_dst, m);
-        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream);
+        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream, h->directed);
         bool host = os.finish(h, m);
         host |= od.finish(h, m);
         if (host) HCUDA(cudaStreamSynchronize(h->stream));
@@ -518,7 +539,7 @@ homln_status homln_or_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity
     if ((or_src == nullptr) != (or_dst == nullptr)) fail(HOMLN_EINVAL, "or_src and or_dst must both be given");
     use_device(h);
     GraphState &g = or_graph(h, layer_mask);
-    const int64_t m = g.csr.nnz / 2;
+    const int64_t m = edge_count(h, g);
     if (or_src) {
         if (capacity < m) {
             *or_edge_count = m;
@@ -527,7 +548,7 @@ homln_status homln_or_aggregate(homln_t h, uint64_t layer_mask, int64_t capacity
         DevOut<int32_t> os, od;
         os.to(h, or_src, m);
         od.to(h, or_dst, m);
-        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream);
+        csr_edge_list(g.csr, os.p, od.p, &h->al, h->stream, h->directed);
         bool host = os.finish(h, m);
         host |= od.finish(h, m);
         if (host) HCUDA(cudaStreamSynchronize(h->stream));
@@ -618,7 +639,7 @@ homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, co
             std::vector<const uint64_t *> sd;
             std::vector<const int32_t *> dg;
             for (int i : ids) {
-                csrs.push_back(&h->layers[i]->csr);
+                csrs.push_back(&in_csr(h, *h->layers[i]));
                 sd.push_back(h->layers[i]->sumdist.p);
                 dg.push_back(h->layers[i]->deg.p);
             }

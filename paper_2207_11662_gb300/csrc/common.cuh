@@ -190,16 +190,20 @@ struct Csr {
 };
 
 // Normalise an edge list (device int32 arrays) into a symmetric CSR with sorted rows.
+// directed: each edge goes into its source's row only (no symmetrisation).
 void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m, Csr &out, int32_t *d_err,
-               Alloc *al, cudaStream_t s);
+               Alloc *al, cudaStream_t s, bool directed = false);
 // Edges present in every CSR of `layers` (sorted-row intersection).
 void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s);
 // Edges present in at least one CSR of `layers` (Boolean OR aggregation).
 void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s);
-// Undirected edge list u < v, ascending (u, v), of a CSR. Writes nnz/2 pairs.
-void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s);
-// Degree-descending relabelling: perm[new] = old; builds the relabelled CSR.
-void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, cudaStream_t s);
+// Edge list ascending (u, v) of a CSR: pairs u < v (nnz/2 of them) of an undirected graph, or
+// every entry of a directed one.
+void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s, bool directed = false);
+// Degree-descending relabelling: perm[new] = old, inv[old] = new; builds the relabelled CSR.
+void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv, Alloc *al, cudaStream_t s);
+// The same relabelling applied to another CSR over the same vertices.
+void relabel_apply(const Csr &g, const int32_t *perm, const int32_t *inv, Csr &out, Alloc *al, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Multi-source BFS (msbfs.cu)
@@ -229,12 +233,16 @@ struct BfsStats {  // filled by an instrumented run
 };
 
 // The graph the BFS traverses: the CSR itself, or its degree-descending relabelling (perm[new] = old).
+// A directed graph also carries its in-edge CSR (csr_in), which the bottom-up levels read.
 struct BfsGraph {
     Csr csr;
+    Csr csr_in;
     DBuf<int32_t> perm;
     bool relabeled = false;
+    bool directed = false;
 };
-void bfs_prepare(const Csr &g, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s);
+// g_in: the in-edge CSR of a directed graph (nullptr when undirected).
+void bfs_prepare(const Csr &g, const Csr *g_in, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s);
 
 struct BfsJob {
     const BfsGraph *g;

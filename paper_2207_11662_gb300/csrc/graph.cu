@@ -14,7 +14,9 @@ namespace {
 constexpr int NODE_BITS = 20;  // HOMLN_MAX_NODES = 2^20
 constexpr uint64_t NODE_MASK = (1ull << NODE_BITS) - 1;
 
-// Degree of each endpoint of every valid, non-loop edge (both directions).
+// Degree of each endpoint of every valid, non-loop edge (both directions; only the source's
+// row when the graph is directed).
+template <bool SYM>
 __global__ void k_count_deg(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m, int32_t n,
                             int32_t *__restrict__ deg, int32_t *err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
@@ -25,18 +27,20 @@ __global__ void k_count_deg(const int32_t *__restrict__ src, const int32_t *__re
         }
         if (a == b) continue;
         atomicAdd(&deg[a], 1);
-        atomicAdd(&deg[b], 1);
+        if (SYM) atomicAdd(&deg[b], 1);
     }
 }
 
-// Each edge lands in both endpoints' rows (row order is fixed later by the row sort).
+// Each edge lands in both endpoints' rows, or only in the source's row when directed
+// (row order is fixed later by the row sort).
+template <bool SYM>
 __global__ void k_scatter_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m, int32_t n,
                                 unsigned long long *__restrict__ cursor, int32_t *__restrict__ col) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = src[e], b = dst[e];
         if (a < 0 || a >= n || b < 0 || b >= n || a == b) continue;
         col[atomicAdd(&cursor[a], 1ull)] = b;
-        col[atomicAdd(&cursor[b], 1ull)] = a;
+        if (SYM) col[atomicAdd(&cursor[b], 1ull)] = a;
     }
 }
 
@@ -156,13 +160,14 @@ __global__ void k_concat_rows(int32_t n, LayerSet L, const int64_t *__restrict__
     }
 }
 
-// Length of the part of row u holding neighbours v > u (rows are sorted).
+// Length of the part of row u holding neighbours v > u (rows are sorted); the whole row when
+// every entry is an edge of its own (directed graphs).
 __global__ void k_upper_len(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            int32_t *__restrict__ len, int64_t *__restrict__ start) {
+                            int32_t *__restrict__ len, int64_t *__restrict__ start, int directed) {
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         int64_t lo = rp[u], hi = rp[u + 1];
         int64_t a = lo, b = hi;
-        while (a < b) {
+        while (!directed && a < b) {
             int64_t mid = (a + b) >> 1;
             if (col[mid] <= u) a = mid + 1; else b = mid;
         }
@@ -190,12 +195,19 @@ __global__ void k_degree_keys(int32_t n, const int64_t *__restrict__ rp, uint64_
     }
 }
 
-__global__ void k_perm_from_keys(int32_t n, const uint64_t *__restrict__ keys, const int64_t *__restrict__ rp,
-                                 int32_t *__restrict__ perm, int32_t *__restrict__ inv, int32_t *__restrict__ newdeg) {
+__global__ void k_perm_from_keys(int32_t n, const uint64_t *__restrict__ keys, int32_t *__restrict__ perm,
+                                 int32_t *__restrict__ inv) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t old = (int32_t)(keys[i] & NODE_MASK);
         perm[i] = old;
         inv[old] = i;
+    }
+}
+
+__global__ void k_perm_degrees(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ perm,
+                               int32_t *__restrict__ newdeg) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t old = perm[i];
         newdeg[i] = (int32_t)(rp[old + 1] - rp[old]);
     }
 }
@@ -215,7 +227,7 @@ int64_t read_i64(const int64_t *d, cudaStream_t s) {
 }  // namespace
 
 void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m, Csr &out, int32_t *d_err, Alloc *al,
-               cudaStream_t s) {
+               cudaStream_t s, bool directed) {
     // degrees -> row offsets -> scatter both directions of every edge -> sort each row ->
     // drop repeated entries (self loops were dropped at the scatter)
     out.n = n;
@@ -229,14 +241,16 @@ void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
     DBuf<int32_t> deg, raw, cnt;
     DBuf<int64_t> rp;
     DBuf<unsigned long long> cursor;
-    if (!deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cursor.alloc(al, n) || !raw.alloc(al, 2 * m) ||
+    if (!deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cursor.alloc(al, n) || !raw.alloc(al, (directed ? 1 : 2) * m) ||
         !cnt.alloc(al, n))
         fail(HOMLN_ENOMEM, "csr scratch");
     HCUDA(cudaMemsetAsync(deg.p, 0, sizeof(int32_t) * n, s));
-    launch(k_count_deg, grid_for(m), 256, 0, s, d_src, d_dst, m, n, deg.p, d_err);
+    if (directed) launch(k_count_deg<false>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, deg.p, d_err);
+    else launch(k_count_deg<true>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, deg.p, d_err);
     scan_exclusive_i32(deg.p, rp.p, n, al, s);
     HCUDA(cudaMemcpyAsync(cursor.p, rp.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
-    launch(k_scatter_edges, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
+    if (directed) launch(k_scatter_edges<false>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
+    else launch(k_scatter_edges<true>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
     sort_rows(n, rp.p, raw.p, al, s);
     launch(k_row_unique<false>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
            (const int32_t *)raw.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr);
@@ -297,40 +311,46 @@ void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc
     HCUDA(cudaGetLastError());
 }
 
-void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s) {
+void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s, bool directed) {
     int32_t n = g.n;
     if (g.nnz == 0) return;
     DBuf<int32_t> len;
     DBuf<int64_t> start, off;
     if (!len.alloc(al, n) || !start.alloc(al, n) || !off.alloc(al, (size_t)n + 1)) fail(HOMLN_ENOMEM, "edge list");
-    launch(k_upper_len, grid_for(n), 256, 0, s, n, g.rowptr.p, g.col.p, len.p, start.p);
+    launch(k_upper_len, grid_for(n), 256, 0, s, n, g.rowptr.p, g.col.p, len.p, start.p, directed ? 1 : 0);
     scan_exclusive_i32(len.p, off.p, n, al, s);
     launch(k_write_pairs, grid_for(n), 256, 0, s, n, g.col.p, start.p, len.p, off.p, d_src, d_dst);
     HCUDA(cudaGetLastError());
 }
 
-void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, Alloc *al, cudaStream_t s) {
+void relabel_apply(const Csr &g, const int32_t *perm, const int32_t *inv, Csr &out, Alloc *al, cudaStream_t s) {
     const int32_t n = g.n;
-    DBuf<uint64_t> vkeys;
-    DBuf<int32_t> inv, newdeg;
-    if (!vkeys.alloc(al, n) || !inv.alloc(al, n) || !newdeg.alloc(al, n) || !perm.alloc(al, n))
-        fail(HOMLN_ENOMEM, "relabel scratch");
-    launch(k_degree_keys, grid_for(n), 256, 0, s, n, g.rowptr.p, vkeys.p);
-    // the keys are generated in id order, so a stable sort on the degree bits alone leaves equal
-    // degrees in ascending id order
-    radix_sort_u64(vkeys.p, nullptr, n, NODE_BITS, 2 * NODE_BITS, al, s);
-    launch(k_perm_from_keys, grid_for(n), 256, 0, s, n, vkeys.p, g.rowptr.p, perm.p, inv.p, newdeg.p);
+    DBuf<int32_t> newdeg;
+    if (!newdeg.alloc(al, n)) fail(HOMLN_ENOMEM, "relabel scratch");
+    launch(k_perm_degrees, grid_for(n), 256, 0, s, n, g.rowptr.p, perm, newdeg.p);
     out.n = n;
     out.nnz = g.nnz;
     if (!out.rowptr.alloc(al, (size_t)n + 1) || !out.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
         fail(HOMLN_ENOMEM, "relabel csr");
     scan_exclusive_i32(newdeg.p, out.rowptr.p, n, al, s);
     if (g.nnz > 0) {
-        launch(k_relabel_rows, grid_for((int64_t)n * 32), 256, 0, s, n, g.rowptr.p, g.col.p, perm.p, inv.p,
+        launch(k_relabel_rows, grid_for((int64_t)n * 32), 256, 0, s, n, g.rowptr.p, g.col.p, perm, inv,
                out.rowptr.p, out.col.p);
         sort_rows(n, out.rowptr.p, out.col.p, al, s);
     }
     HCUDA(cudaGetLastError());
+}
+
+void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv, Alloc *al, cudaStream_t s) {
+    const int32_t n = g.n;
+    DBuf<uint64_t> vkeys;
+    if (!vkeys.alloc(al, n) || !inv.alloc(al, n) || !perm.alloc(al, n)) fail(HOMLN_ENOMEM, "relabel scratch");
+    launch(k_degree_keys, grid_for(n), 256, 0, s, n, g.rowptr.p, vkeys.p);
+    // the keys are generated in id order, so a stable sort on the degree bits alone leaves equal
+    // degrees in ascending id order
+    radix_sort_u64(vkeys.p, nullptr, n, NODE_BITS, 2 * NODE_BITS, al, s);
+    launch(k_perm_from_keys, grid_for(n), 256, 0, s, n, vkeys.p, perm.p, inv.p);
+    relabel_apply(g, perm.p, inv.p, out, al, s);
 }
 
 }  // namespace homln

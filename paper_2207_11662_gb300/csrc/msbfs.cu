@@ -30,8 +30,10 @@ namespace homln {
 namespace {
 
 struct GraphDesc {
-    const int64_t *rowptr;
+    const int64_t *rowptr;  // out-edges: top-down levels push along them
     const int32_t *col;
+    const int64_t *prow;    // in-edges: bottom-up levels pull along them (the same CSR if undirected)
+    const int32_t *pcol;
     uint64_t *F;
     uint32_t *R;
     int32_t n;
@@ -75,8 +77,10 @@ __device__ __forceinline__ int32_t first_below(const int64_t *__restrict__ rp, i
 
 // One tile as seen by one block: the graph, the team's state, the block's place in the team.
 struct Tile {
-    const int64_t *__restrict__ rowptr;
+    const int64_t *__restrict__ rowptr;  // out-edges (push)
     const int32_t *__restrict__ col;
+    const int64_t *__restrict__ prow;    // in-edges (pull)
+    const int32_t *__restrict__ pcol;
     uint64_t *seen;
     uint64_t *acc;
     uint8_t *quiet;
@@ -240,7 +244,7 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
     int64_t it = 0;
     int32_t u[U];
 #pragma unroll
-    for (int i = 0; i < U; ++i) u[i] = (j + (int64_t)i * S < re) ? __ldg(a.col + j + (int64_t)i * S) : -1;
+    for (int i = 0; i < U; ++i) u[i] = (j + (int64_t)i * S < re) ? __ldg(a.pcol + j + (int64_t)i * S) : -1;
     while (true) {
         uint64_t f[U][K];
 #pragma unroll
@@ -257,7 +261,7 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
         const int64_t here = (min(re, jn) - j + S - 1) / S;
         if (more) {
 #pragma unroll
-            for (int i = 0; i < U; ++i) u[i] = (jn + (int64_t)i * S < re) ? __ldg(a.col + jn + (int64_t)i * S) : -1;
+            for (int i = 0; i < U; ++i) u[i] = (jn + (int64_t)i * S < re) ? __ldg(a.pcol + jn + (int64_t)i * S) : -1;
         }
 #pragma unroll
         for (int i = 0; i < U; ++i)
@@ -287,7 +291,7 @@ __device__ __forceinline__ int64_t gather_or_warp(const Tile &a, const uint64_t 
         for (int i = 0; i < U; ++i) {
             const int64_t jj = j + (int64_t)i * S;
             if (jj < re) {
-                ldw<K>(cur + (int64_t)__ldg(a.col + jj) * W + q * K, f[i]);
+                ldw<K>(cur + (int64_t)__ldg(a.pcol + jj) * W + q * K, f[i]);
                 ++it;
             } else {
 #pragma unroll
@@ -500,7 +504,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 lane_need |= need[k] != 0;
             }
             const bool full0 = __syncthreads_or(lane_need ? 1 : 0) == 0;
-            const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
+            const int64_t rb = a.prow[v], re = a.prow[v + 1];
             int64_t it = 0;
             if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
             if (STATS) {
@@ -552,7 +556,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 lane_need |= need[k] != 0;
             }
             const bool full0 = !__any_sync(0xffffffffu, lane_need);
-            const int64_t rb = a.rowptr[v], re = a.rowptr[v + 1];
+            const int64_t rb = a.prow[v], re = a.prow[v + 1];
             int64_t it = 0;
 #if HOMLN_WARP_COORD
             if (!full0) it = gather_or_warp<W>(a, cur, rb, re, q, need, acc);
@@ -607,8 +611,8 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                         need[k] = ~s[k];
                         lane_need |= need[k] != 0;
                     }
-                    rb = a.rowptr[v];
-                    re = a.rowptr[v + 1];
+                    rb = a.prow[v];
+                    re = a.prow[v + 1];
                 }
                 // every lane must take part in the shuffle, so no short-circuit around it
                 const bool group_needs = group_any<T>(lane_need);
@@ -769,6 +773,8 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         Tile a;
         a.rowptr = g.rowptr;
         a.col = g.col;
+        a.prow = g.prow;
+        a.pcol = g.pcol;
         a.seen = seen;
         a.acc = acc;
         a.quiet = quiet;
@@ -778,9 +784,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         a.n = g.n;
         // hub tiers: rows of at least 4 iterations per slot go to a whole block / a whole warp
         a.hub_block_end =
-            g.by_degree ? first_below(g.rowptr, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+            g.by_degree ? first_below(g.prow, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
         a.hub_warp_end = g.by_degree
-                             ? max(a.hub_block_end, first_below(g.rowptr, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                             ? max(a.hub_block_end, first_below(g.prow, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
                              : 0;
         a.rank = rank;
         a.tsize = tsize;
@@ -824,6 +830,8 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     Tile a;
     a.rowptr = g.rowptr;
     a.col = g.col;
+    a.prow = g.prow;
+    a.pcol = g.pcol;
     a.seen = A.state;
     a.acc = A.state + 3 * arr;
     a.quiet = A.quiet;
@@ -832,9 +840,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.ctr = A.ctr;
     a.n = g.n;
     a.hub_block_end =
-            g.by_degree ? first_below(g.rowptr, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+            g.by_degree ? first_below(g.prow, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
     a.hub_warp_end = g.by_degree
-                         ? max(a.hub_block_end, first_below(g.rowptr, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                         ? max(a.hub_block_end, first_below(g.prow, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
                          : 0;
     a.rank = blockIdx.x;
     a.tsize = gridDim.x;
@@ -985,6 +993,8 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
         d.by_degree = G.relabeled ? 1 : 0;
         d.rowptr = G.csr.rowptr.p;
         d.col = G.csr.col.p;
+        d.prow = G.directed ? G.csr_in.rowptr.p : G.csr.rowptr.p;
+        d.pcol = G.directed ? G.csr_in.col.p : G.csr.col.p;
         if (G.relabeled) {
             if (!Fi[i].alloc(al, d.n) || !Ri[i].alloc(al, d.n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
             d.F = Fi[i].p;
@@ -1094,18 +1104,31 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     }
 }
 
-void bfs_prepare(const Csr &g, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s) {
+static void copy_csr(const Csr &g, Csr &out, Alloc *al, cudaStream_t s) {
+    out.n = g.n;
+    out.nnz = g.nnz;
+    if (!out.rowptr.alloc(al, (size_t)g.n + 1) || !out.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
+        fail(HOMLN_ENOMEM, "bfs graph");
+    HCUDA(cudaMemcpyAsync(out.rowptr.p, g.rowptr.p, sizeof(int64_t) * (g.n + 1), cudaMemcpyDeviceToDevice, s));
+    if (g.nnz > 0)
+        HCUDA(cudaMemcpyAsync(out.col.p, g.col.p, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToDevice, s));
+}
+
+void bfs_prepare(const Csr &g, const Csr *g_in, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s) {
+    // the vertex order follows the degrees of the graph the bottom-up levels read (in-edges)
     out.relabeled = relabel;
+    out.directed = g_in != nullptr;
     if (relabel) {
-        relabel_by_degree(g, out.csr, out.perm, al, s);
+        DBuf<int32_t> inv;
+        if (out.directed) {
+            relabel_by_degree(*g_in, out.csr_in, out.perm, inv, al, s);
+            relabel_apply(g, out.perm.p, inv.p, out.csr, al, s);
+        } else {
+            relabel_by_degree(g, out.csr, out.perm, inv, al, s);
+        }
     } else {  // the BFS reads the graph as it is
-        out.csr.n = g.n;
-        out.csr.nnz = g.nnz;
-        if (!out.csr.rowptr.alloc(al, (size_t)g.n + 1) || !out.csr.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
-            fail(HOMLN_ENOMEM, "bfs graph");
-        HCUDA(cudaMemcpyAsync(out.csr.rowptr.p, g.rowptr.p, sizeof(int64_t) * (g.n + 1), cudaMemcpyDeviceToDevice, s));
-        if (g.nnz > 0)
-            HCUDA(cudaMemcpyAsync(out.csr.col.p, g.col.p, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToDevice, s));
+        copy_csr(g, out.csr, al, s);
+        if (out.directed) copy_csr(*g_in, out.csr_in, al, s);
     }
 }
 

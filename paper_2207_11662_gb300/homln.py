@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhomln.so")
 
 HOMLN_OK, HOMLN_EINVAL, HOMLN_ENOMEM, HOMLN_ECUDA, HOMLN_ERANGE, HOMLN_ETIMEOUT, HOMLN_EBUSY = range(7)
-HOMLN_PTR_HOST, HOMLN_PTR_DEVICE = 0, 1
+HOMLN_PTR_HOST, HOMLN_PTR_DEVICE, HOMLN_DIRECTED = 0, 1, 2
 HOMLN_NAIVE, HOMLN_CC1, HOMLN_CC2 = 0, 1, 2
 HOMLN_TOPK_PERCENT, HOMLN_TOPK_COUNT, HOMLN_GE_MEAN, HOMLN_GT_MEAN = 0, 1, 2, 3
 MAX_NODES = 1 << 20
@@ -179,7 +179,8 @@ def torch_allocator():
 # C-named functions (raw handles)
 # ---------------------------------------------------------------------------
 
-def homln_create(n_nodes: int, layers, flags: int | None = None, allocator=None, stream=None) -> int:
+def homln_create(n_nodes: int, layers, flags: int | None = None, allocator=None, stream=None,
+                 directed: bool = False) -> int:
     """layers: list of (src, dst) int32 arrays/tensors. flags defaults to DEVICE if they are CUDA tensors."""
     L = len(layers)
     counts = (c_int64 * max(L, 1))(*[int(s.shape[0]) for s, _ in layers])
@@ -187,6 +188,8 @@ def homln_create(n_nodes: int, layers, flags: int | None = None, allocator=None,
     dsts = (c_void_p * max(L, 1))(*[ptr(d) for _, d in layers])
     if flags is None:
         flags = HOMLN_PTR_DEVICE if L and getattr(layers[0][0], "is_cuda", False) else HOMLN_PTR_HOST
+    if directed:
+        flags |= HOMLN_DIRECTED
     out = c_void_p()
     rc = lib.homln_create(int(n_nodes), L, counts, srcs, dsts, int(flags),
                           ctypes.byref(allocator) if allocator is not None else None,
@@ -320,7 +323,8 @@ def homln_version() -> str:
 class Network:
     """One HoMLN resident on a GPU. Outputs are torch CUDA tensors (farness int64, reach int32)."""
 
-    def __init__(self, n: int, layers, device=None, stream=None, allocator=None, tuning: dict | None = None):
+    def __init__(self, n: int, layers, device=None, stream=None, allocator=None, tuning: dict | None = None,
+                 directed: bool = False):
         import torch
         self.torch = torch
         self.n = int(n)
@@ -330,7 +334,7 @@ class Network:
         self.stream = stream
         self._alloc = allocator
         with torch.cuda.device(self.device):
-            self.h = homln_create(self.n, layers, allocator=allocator, stream=stream)
+            self.h = homln_create(self.n, layers, allocator=allocator, stream=stream, directed=directed)
         self.n_layers = len(layers)
         if tuning:
             homln_set_tuning(self.h, **tuning)

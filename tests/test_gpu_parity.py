@@ -44,9 +44,9 @@ def check_graph(gF, gR, gcc, ref):
     assert np.array_equal(cc, ref["cc"]), np.max(np.abs(cc - ref["cc"]))
 
 
-def full_parity(H, net, sels, tuning=None, heuristics=(0, 1, 2)):
-    g = H.Network(net.n, to_dev(net.layers), tuning=tuning)
-    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+def full_parity(H, net, sels, tuning=None, heuristics=(0, 1, 2), directed=False):
+    g = H.Network(net.n, to_dev(net.layers), tuning=tuning, directed=directed)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8, directed=directed)
     L = net.n_layers
     for i in range(L):
         check_graph(*g.layer_closeness(i), ref.layer(i))
@@ -194,6 +194,64 @@ def test_or_aggregation(H):
         check_graph(*g.or_closeness(mask), ref.or_graph(mask))
         out = g.topk(-2, mask, sel)
         assert out.cpu().numpy().tolist() == ref.topk(-2, mask, osel).tolist()
+    g.close()
+
+
+def directed_net(n=1500, avg=6.0, L=3, rho=0.4, seed=91, recip=0.25):
+    net = synth.homln_small_overlap(n, avg, L, rho, seed)
+    return synth.HoMLN(n, [synth.with_reciprocal(e, recip, seed + i) for i, e in enumerate(net.layers)])
+
+
+@pytest.mark.parametrize("W,alpha,relabel", [(8, 16, 1), (2, 1, 0), (1, 1000000, 1), (32, 16, 0)])
+def test_directed_layers(H, W, alpha, relabel):
+    """Directed layers (in-closeness): pull along in-edges, push along out-edges, in-degree CC1."""
+    full_parity(H, directed_net(), sels_all(H)[:2], directed=True,
+                tuning=dict(words_per_node=W, push_alpha=alpha, relabel=relabel))
+
+
+def test_batch_analyse_mixes_directed_and_undirected(H):
+    """One persistent launch over the tiles of a directed and an undirected HoMLN."""
+    nets = [directed_net(900, 5.0, 2, 0.3, 81), synth.homln_small_overlap(700, 6.0, 3, 0.4, 82)]
+    kinds = [True, False]
+    gs = [H.Network(net.n, to_dev(net.layers), directed=dr) for net, dr in zip(nets, kinds)]
+    masks = [(1 << net.n_layers) - 1 for net in nets]
+    H.homln_batch_analyse([g.h for g in gs], masks, True)
+    for g, net, mask, dr in zip(gs, nets, masks, kinds):
+        ref = O.OracleHoMLN(net.n, net.layers, threads=8, directed=dr)
+        for i in range(net.n_layers):
+            check_graph(*g.layer_closeness(i), ref.layer(i))
+        check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+        g.close()
+
+
+def test_directed_or_hubs_and_closed_forms(H):
+    """Directed OR graphs, an in-star and an out-star (hub tiers on the in-CSR), a directed path and cycle."""
+    n = 3000
+    path = (np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32))
+    cyc = (np.arange(n, dtype=np.int32), ((np.arange(n) + 1) % n).astype(np.int32))
+    g = H.Network(n, to_dev([path, cyc]), directed=True)
+    F, R, _ = g.layer_closeness(0)
+    i = np.arange(n, dtype=np.int64)
+    assert np.array_equal(F.cpu().numpy(), i * (i + 1) // 2) and np.array_equal(R.cpu().numpy(), i)
+    F, R, _ = g.layer_closeness(1)
+    assert np.all(F.cpu().numpy() == n * (n - 1) // 2) and np.all(R.cpu().numpy() == n - 1)
+    g.close()
+    n = 5000
+    into = (np.arange(1, n, dtype=np.int32), np.zeros(n - 1, np.int32))
+    outof = (np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32))
+    cl = synth.chung_lu_edges(n, 25000, 78)
+    net = synth.HoMLN(n, [synth.overlay(n, into, cl), synth.overlay(n, outof, cl), cl])
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    for W in (2, 16):
+        full_parity(H, net, sel, directed=True, tuning=dict(words_per_node=W, threads=256))
+    dn = directed_net(1200, 5.0, 3, 0.3, 72)
+    ref = O.OracleHoMLN(dn.n, dn.layers, threads=8, directed=True)
+    g = H.Network(dn.n, to_dev(dn.layers), directed=True)
+    for mask in (7, 5):
+        s, d = g.or_aggregate(mask)
+        rs, rd = ref.or_edges(mask)
+        assert np.array_equal(s.cpu().numpy(), rs) and np.array_equal(d.cpu().numpy(), rd)
+        check_graph(*g.or_closeness(mask), ref.or_graph(mask))
     g.close()
 
 
