@@ -100,8 +100,9 @@ typedef struct homln_select {
 
 /* Device-memory allocator. alloc returns device memory usable on `stream`
  * (or NULL on failure); free releases it in stream order. NULL for the whole
- * struct selects cudaMallocAsync/cudaFreeAsync. The library calls it from the
- * thread that called into the library. */
+ * struct selects a stream-ordered memory pool owned by the library, one per
+ * device, that keeps up to 8 GiB of freed memory mapped for later calls. The
+ * library calls it from the thread that called into the library. */
 typedef struct homln_allocator {
     void *ctx;
     void *(*alloc)(void *ctx, size_t bytes, void *stream);

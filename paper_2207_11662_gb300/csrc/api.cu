@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <tuple>
 
@@ -32,11 +33,45 @@ void check_cuda(cudaError_t e, const char *what) {
     }
 }
 
+// Without a caller allocator, device memory comes from one stream-ordered pool per device
+// owned by the library. The pool keeps up to kPoolKeepBytes of freed memory mapped across
+// synchronisations, so the BFS state and the scratch of repeated calls are not unmapped and
+// mapped again every call (a pool with the default threshold of 0 returns it at every sync).
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+constexpr int kMaxDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[kMaxDevices];
+
+static cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
 void *Alloc::get(size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (a.alloc) return a.alloc(a.ctx, bytes, (void *)stream);
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaMemPool_t pool = device_pool();
+    if (!pool) return nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }

@@ -916,18 +916,22 @@ BfsKernel kernel_for(int W, bool stats) {
     }
 }
 
-// Bytes of BFS state across all teams. Measured on the 50,000-node power-law workload:
-// 8 teams x W=8 and 4 teams x W=16 (both 102 MB) beat every 51 MB split, so the budget
-// lets the state exceed L2 a little; the frontier gathers still mostly hit in L2.
-constexpr double kStateBudget = 104.0e6;
-constexpr int kMaxTeams = 16;
+// Widest tile: one team's state (4 arrays of n x W words) stays within this many bytes.
+constexpr double kWordsBudget = 104.0e6;
+// Default teams, measured on GB300 (W = 8, 304 blocks): 12 teams were best or within noise of
+// it on both the 50,000-node power-law workload (8 teams: 3% slower) and the 200,000-node BA
+// workload (2 teams: 24% slower, 24 teams: 4% slower). The frontier gathers of more teams
+// than fit L2 still hit L2 mostly, and smaller teams meet at their barriers sooner. The
+// state of all teams is capped at kStateCap bytes.
+constexpr int kDefaultTeams = 12;
+constexpr double kStateCap = 2.0e9;
 
 }  // namespace
 
 int msbfs_pick_words(int32_t n, int64_t nnz) {
     (void)nnz;
     int W = 32;
-    while (W > 1 && 4.0 * n * 8.0 * W > kStateBudget) W >>= 1;
+    while (W > 1 && 4.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
     while (W > 1 && (int64_t)64 * (W / 2) >= n) W >>= 1;  // no wider than the node count needs
     return W;
 }
@@ -947,16 +951,17 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
 
     const bool plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
-    // Defaults, measured on GB300: 8 words per node (512 sources per tile) with as many teams as
-    // the state budget allows, at most 16 (8 teams at n = 50,000, 2 at n = 200,000).
-    int W = t.W > 0 ? t.W : std::min(8, msbfs_pick_words(maxn, maxnnz));
+    // Defaults, measured on GB300: 8 words per node (512 sources per tile), 12 teams.
+    // The plain schedule (one team, the host driving every level) takes the widest tile the
+    // budget allows, which needs the fewest launches and host round trips.
+    int W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn, maxnnz) : std::min(8, msbfs_pick_words(maxn, maxnnz));
     int nteams = 1;
     if (!plain) {
         if (t.teams > 0) {
             nteams = t.teams;
         } else {
-            nteams = (int)std::floor(kStateBudget / (4.0 * maxn * 8.0 * W));
-            nteams = std::max(1, std::min(kMaxTeams, nteams));
+            nteams = (int)std::floor(kStateCap / (4.0 * maxn * 8.0 * W));
+            nteams = std::max(1, std::min(kDefaultTeams, nteams));
             int64_t tiles = 0;  // no more teams than tiles
             for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
             if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);

@@ -55,13 +55,15 @@ class Request:
 
 def footprint_bytes(n: int, edge_counts) -> int:
     """Estimated peak device bytes of one request: the layer CSRs and their relabelled copies,
-    the AND graph, the construction scratch and the per-graph outputs."""
+    the AND graph, the construction scratch, the per-graph outputs and the BFS state (12 teams
+    of 4 arrays of n x 8 words at most)."""
     m = int(sum(edge_counts))
     L = len(edge_counts)
     csr = 2 * (8 * (n + 1) * (L + 1) + 8 * m)  # rowptr + col (symmetric), original and relabelled
     build = 8 * 2 * max(edge_counts, default=0) * 3  # sort keys, alternate keys, flags of one layer
     outputs = (L + 1) * n * (8 + 4 + 8 + 8 + 4)
-    return int(csr + build + outputs + (1 << 20))
+    bfs_state = 12 * 4 * 8 * 8 * n
+    return int(csr + build + outputs + bfs_state + (1 << 20))
 
 
 class Admission:
