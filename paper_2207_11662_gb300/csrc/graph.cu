@@ -91,18 +91,27 @@ struct LayerSet {
     int r;
 };
 
-__device__ __forceinline__ bool row_contains(const int32_t *__restrict__ col, int64_t lo, int64_t hi, int32_t x) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        int32_t c = col[mid];
-        if (c == x) return true;
-        if (c < x) lo = mid + 1; else hi = mid;
+// Which lanes' candidates v (ascending over the valid lanes [0, nv)) occur in the sorted row
+// col[lo, hi): the warp walks the row 32 entries at a time, skips chunks outside the
+// candidates' range, and compares every candidate with every entry of a chunk by shuffles.
+__device__ __forceinline__ bool warp_row_has(const int32_t *__restrict__ col, int64_t lo, int64_t hi, int32_t v,
+                                             int nv, int lane) {
+    const int32_t vmin = __shfl_sync(0xffffffffu, v, 0), vmax = __shfl_sync(0xffffffffu, v, nv - 1);
+    bool hit = false;
+    for (int64_t c = lo; c < hi; c += 32) {
+        const int64_t j = c + lane;
+        const int32_t w = j < hi ? __ldg(col + j) : INT32_MAX;
+        const int last = (int)(hi - 1 - c < 31 ? hi - 1 - c : 31);
+        const int32_t wmin = __shfl_sync(0xffffffffu, w, 0), wmax = __shfl_sync(0xffffffffu, w, last);
+        if (wmax < vmin) continue;
+        if (wmin > vmax) break;
+        for (int k = 0; k <= last; ++k) hit |= __shfl_sync(0xffffffffu, w, k) == v;
     }
-    return false;
+    return hit && lane < nv;
 }
 
-// One warp per vertex: the lanes walk the shortest of its rows 32 entries at a time and keep
-// the entries found (binary search) in every other row; a ballot keeps them in order.
+// One warp per vertex: the lanes take the shortest of its rows 32 entries at a time and keep
+// the entries present in every other row; a ballot keeps them in order.
 template <bool WRITE>
 __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, const int64_t *__restrict__ out_rp,
                            int32_t *__restrict__ out_col) {
@@ -121,13 +130,15 @@ __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, con
         int32_t c = 0;
         for (int64_t j0 = 0; j0 < best_len; j0 += 32) {
             const int64_t j = j0 + lane;
-            bool all = false;
-            int32_t v = 0;
-            if (j < best_len) {
-                v = L.col[best][b0 + j];
-                all = true;
-                for (int i = 0; i < L.r && all; ++i)
-                    if (i != best) all = row_contains(L.col[i], L.rp[i][u], L.rp[i][u + 1], v);
+            const int nv = (int)(best_len - j0 < 32 ? best_len - j0 : 32);
+            const int32_t v = j < best_len ? __ldg(L.col[best] + b0 + j) : -1;
+            bool all = lane < nv;
+            for (int i = 0; i < L.r; ++i) {
+                if (i == best) continue;
+                if (!__any_sync(0xffffffffu, all)) break;
+                // every lane takes part in the shuffles, so no short-circuit around the call
+                const bool has = warp_row_has(L.col[i], L.rp[i][u], L.rp[i][u + 1], v, nv, lane);
+                all = all && has;
             }
             const uint32_t m = __ballot_sync(0xffffffffu, all);
             if (WRITE && all) out_col[o + c + __popc(m & ((1u << lane) - 1u))] = v;

@@ -130,46 +130,75 @@ void scan_impl(const T *in, int64_t *out, int64_t n, Alloc *al, cudaStream_t s) 
 }
 
 // ---------------------------------------------------------------------------
-// Radix sort: 8-bit digits, one histogram / scan / scatter round per digit.
-// The scatter ranks each tile's items stably: every warp walks its 512 items
+// Radix sort: 8-bit digits, one histogram / offsets / scatter round per digit.
+// The scatter ranks each tile's items stably: every warp walks its R*32 items
 // in index order, 32 at a time, grouping equal digits with match.any.
+// Small inputs (at most kRsFusedTiles tiles) skip the separate scan: every
+// scatter block derives its own digit offsets from the per-tile histograms.
 // ---------------------------------------------------------------------------
 constexpr int RS_T = 256;
 constexpr int RS_WARPS = RS_T / 32;
-constexpr int RS_R = 16;  // rounds per warp
-constexpr int RS_TILE = RS_T * RS_R;
+constexpr int kRsFusedTiles = 64;
 
+template <int R>
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
                                                  uint32_t dmask, int32_t *counts, int64_t nb) {
     __shared__ int32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int i = threadIdx.x; i < RS_TILE; i += RS_T) {
-        int64_t idx = base + i;
+    const int64_t base = (int64_t)blockIdx.x * (RS_T * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t idx = base + r * RS_T + threadIdx.x;
         if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & dmask], 1);
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-template <bool VALS>
+// FUSED: offsets[] holds the per-tile histograms (digit-major, counts[d * nb + b]) and each
+// block computes its tile's digit offsets from them; otherwise offsets[] is their scan.
+template <bool VALS, int R, bool FUSED>
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
                                                     int shift, uint32_t dmask, const int64_t *__restrict__ offsets,
-                                                    int64_t nb) {
+                                                    const int32_t *__restrict__ counts, int64_t nb) {
     __shared__ int32_t wcnt[RS_WARPS][256];
     __shared__ int64_t boff[256];
+    __shared__ int64_t wtot[RS_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_T) (&wcnt[0][0])[i] = 0;
-    boff[threadIdx.x] = offsets[(int64_t)threadIdx.x * nb + blockIdx.x];
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_R * 32);
-    uint64_t k[RS_R];
-    uint32_t v[RS_R];
-    int32_t rank[RS_R];
+    if (FUSED) {
+        // digit d = threadIdx.x: items of digit d in all tiles, and in the tiles before this one
+        const int32_t *row = counts + (int64_t)threadIdx.x * nb;
+        int64_t tot = 0, pre = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int32_t c = row[b];
+            tot += c;
+            if (b < blockIdx.x) pre += c;
+        }
+        // exclusive scan of the digit totals over the block
+        int64_t x = tot;
 #pragma unroll
-    for (int r = 0; r < RS_R; ++r) {
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        int64_t wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += wtot[w];
+        boff[threadIdx.x] = wbase + x - tot + pre;
+    } else {
+        boff[threadIdx.x] = offsets[(int64_t)threadIdx.x * nb + blockIdx.x];
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * (RS_T * R) + (int64_t)warp * (R * 32);
+    uint64_t k[R];
+    uint32_t v[R];
+    int32_t rank[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
         int64_t idx = base + r * 32 + lane;
         bool valid = idx < n;
         k[r] = valid ? kin[idx] : 0ull;
@@ -197,7 +226,7 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict_
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RS_R; ++r) {
+    for (int r = 0; r < R; ++r) {
         int64_t idx = base + r * 32 + lane;
         if (idx < n) {
             uint32_t d = (uint32_t)((k[r] >> shift) & dmask);
@@ -206,6 +235,19 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict_
             if (VALS) vout[dest] = v[r];
         }
     }
+}
+
+template <int R, bool FUSED>
+void rs_pass(const uint64_t *ka, const uint32_t *va, uint64_t *kb, uint32_t *vb, int64_t n, int shift,
+             uint32_t dmask, int32_t *counts, int64_t *offs, int64_t nb, Alloc *al, cudaStream_t s) {
+    launch(k_rs_hist<R>, (unsigned)nb, RS_T, 0, s, ka, n, shift, dmask, counts, nb);
+    if (!FUSED) scan_impl<int32_t>(counts, offs, 256 * nb, al, s);
+    if (va)
+        launch(k_rs_scatter<true, R, FUSED>, (unsigned)nb, RS_T, 0, s, ka, va, kb, vb, n, shift, dmask,
+               (const int64_t *)offs, (const int32_t *)counts, nb);
+    else
+        launch(k_rs_scatter<false, R, FUSED>, (unsigned)nb, RS_T, 0, s, ka, (const uint32_t *)nullptr, kb,
+               (uint32_t *)nullptr, n, shift, dmask, (const int64_t *)offs, (const int32_t *)counts, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -232,30 +274,37 @@ __device__ __forceinline__ int32_t warp_bitonic_sort(int32_t x) {
     return x;
 }
 
-__global__ void k_sort_rows_small(int32_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ col) {
+// Rows of <= 32 entries are sorted here; longer rows are listed for the block sort (mid[],
+// up to kRowSortSmem entries) or the radix fallback (big[]).
+__global__ void k_sort_rows_small(int32_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ col,
+                                  int32_t *__restrict__ mid, int32_t *__restrict__ big, int32_t *__restrict__ nlist) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < n; r += nwarps) {
         const int64_t b = rp[r], d = rp[r + 1] - b;
-        if (d < 2 || d > 32) continue;  // uniform over the warp
+        if (d > 32) {  // uniform over the warp
+            if (lane == 0) {
+                if (d <= kRowSortSmem) mid[atomicAdd(&nlist[0], 1)] = (int32_t)r;
+                else big[atomicAdd(&nlist[1], 1)] = (int32_t)r;
+            }
+            continue;
+        }
+        if (d < 2) continue;
         int32_t x = lane < d ? col[b + lane] : INT32_MAX;
         x = warp_bitonic_sort(x);
         if (lane < d) col[b + lane] = x;
     }
 }
 
-// One block per row of 33 .. kRowSortSmem entries; rows longer than that are listed in big[].
-__global__ void __launch_bounds__(256) k_sort_rows_mid(int32_t n, const int64_t *__restrict__ rp,
-                                                       int32_t *__restrict__ col, int32_t *big, int32_t *nbig) {
+// One block per listed row of 33 .. kRowSortSmem entries.
+__global__ void __launch_bounds__(256) k_sort_rows_mid(const int64_t *__restrict__ rp, int32_t *__restrict__ col,
+                                                       const int32_t *__restrict__ mid, const int32_t *__restrict__ nlist) {
     __shared__ int32_t sh[kRowSortSmem];
-    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const int32_t count = nlist[0];
+    for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
+        const int32_t r = mid[li];
         const int64_t b = rp[r], d = rp[r + 1] - b;
-        if (d <= 32) continue;  // uniform over the block
-        if (d > kRowSortSmem) {
-            if (threadIdx.x == 0) big[atomicAdd(nbig, 1)] = (int32_t)r;
-            continue;
-        }
         int P = 64;
         while (P < d) P <<= 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < d ? col[b + i] : INT32_MAX;
@@ -308,25 +357,29 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, Alloc *al, c
 
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit1, Alloc *al, cudaStream_t s) {
     if (n <= 1 || bit1 <= bit0) return;
-    int64_t nb = ceil_div(n, RS_TILE);
+    // tile of 4 items per thread while that keeps the tiles few enough for the fused offsets,
+    // else 16 per thread; beyond kRsFusedTiles tiles of 16 a separate scan makes the offsets
+    const int R = n <= (int64_t)kRsFusedTiles * RS_T * 4 ? 4 : 16;
+    const int64_t nb = ceil_div(n, (int64_t)RS_T * R);
+    const bool fused = nb <= kRsFusedTiles;
     DBuf<uint64_t> kalt;
     DBuf<uint32_t> valt;
     DBuf<int32_t> counts;
     DBuf<int64_t> offs;
     if (!kalt.alloc(al, n) || (vals && !valt.alloc(al, n)) || !counts.alloc(al, 256 * nb) ||
-        !offs.alloc(al, 256 * nb + 1))
+        (!fused && !offs.alloc(al, 256 * nb + 1)))
         fail(HOMLN_ENOMEM, "radix sort scratch");
     uint64_t *ka = keys, *kb = kalt.p;
     uint32_t *va = vals, *vb = valt.p;
     for (int shift = bit0; shift < bit1; shift += 8) {
         int bits = bit1 - shift < 8 ? bit1 - shift : 8;
         uint32_t dmask = (1u << bits) - 1u;
-        launch(k_rs_hist, (unsigned)nb, RS_T, 0, s, ka, n, shift, dmask, counts.p, nb);
-        scan_exclusive_i32(counts.p, offs.p, 256 * nb, al, s);
-        if (vals)
-            launch(k_rs_scatter<true>, (unsigned)nb, RS_T, 0, s, ka, va, kb, vb, n, shift, dmask, offs.p, nb);
+        if (R == 4)
+            rs_pass<4, true>(ka, va, kb, vb, n, shift, dmask, counts.p, offs.p, nb, al, s);
+        else if (fused)
+            rs_pass<16, true>(ka, va, kb, vb, n, shift, dmask, counts.p, offs.p, nb, al, s);
         else
-            launch(k_rs_scatter<false>, (unsigned)nb, RS_T, 0, s, ka, nullptr, kb, nullptr, n, shift, dmask, offs.p, nb);
+            rs_pass<16, false>(ka, va, kb, vb, n, shift, dmask, counts.p, offs.p, nb, al, s);
         HCUDA(cudaGetLastError());
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -339,13 +392,17 @@ void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit
 
 void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cudaStream_t s) {
     if (n <= 0) return;
-    DBuf<int32_t> big, nbig;
-    if (!big.alloc(al, n) || !nbig.alloc(al, 1)) fail(HOMLN_ENOMEM, "row sort scratch");
-    HCUDA(cudaMemsetAsync(nbig.p, 0, sizeof(int32_t), s));
-    launch(k_sort_rows_small, grid_of((int64_t)n * 32, 256), 256, 0, s, n, d_rowptr, d_col);
-    launch(k_sort_rows_mid, (unsigned)std::min<int64_t>(n, 65535 * 4), 256, 0, s, n, d_rowptr, d_col, big.p, nbig.p);
+    DBuf<int32_t> mid, big, nlist;
+    if (!mid.alloc(al, n) || !big.alloc(al, n) || !nlist.alloc(al, 2)) fail(HOMLN_ENOMEM, "row sort scratch");
+    HCUDA(cudaMemsetAsync(nlist.p, 0, 2 * sizeof(int32_t), s));
+    launch(k_sort_rows_small, grid_of((int64_t)n * 32, 256), 256, 0, s, n, d_rowptr, d_col, mid.p, big.p, nlist.p);
+    int dev = 0, nsm = 0;
+    HCUDA(cudaGetDevice(&dev));
+    HCUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    launch(k_sort_rows_mid, (unsigned)(nsm * 4), 256, 0, s, (const int64_t *)d_rowptr, d_col, (const int32_t *)mid.p,
+           (const int32_t *)nlist.p);
     int32_t h_nbig = 0;
-    HCUDA(cudaMemcpyAsync(&h_nbig, nbig.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaMemcpyAsync(&h_nbig, nlist.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HCUDA(cudaStreamSynchronize(s));
     if (h_nbig == 0) return;
     std::vector<int32_t> rows(h_nbig);

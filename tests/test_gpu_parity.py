@@ -295,6 +295,17 @@ def test_degenerate_graphs(H):
     full_parity(H, synth.HoMLN(n, [e, synth.noisy_copy(n, e, 4)]), sel)
 
 
+def test_many_nodes_small_components(H):
+    """300,000 nodes in small components (average degree 0.8): the relabelling and selection
+    sorts take the multi-block radix path with a separate scan (more than 64 tiles of 4,096)."""
+    n = 300000
+    a = synth.er_edges(n, 90000, 31)
+    net = synth.HoMLN(n, [synth.overlay(n, a, synth.er_edges(n, 30000, 32)), synth.overlay(n, a, synth.er_edges(n, 30000, 33))])
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)),
+           (H.make_select(H.HOMLN_GE_MEAN), O.Select(O.GE_MEAN))]
+    full_parity(H, net, sel, heuristics=(0, 2))
+
+
 def test_path_and_cycle_closed_forms(H):
     """Long diameters (thousands of levels) against the closed forms directly."""
     n = 3000
