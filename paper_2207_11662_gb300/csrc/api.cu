@@ -169,7 +169,10 @@ void use_device(homln_t h) { HCUDA(cudaSetDevice(h->device)); }
 // The CSR whose rows are the neighbours that reach a vertex: the in-edges of a directed graph.
 const Csr &in_csr(homln_t h, const GraphState &g) { return h->directed ? g.csr_in : g.csr; }
 
-int64_t edge_count(homln_t h, const GraphState &g) { return h->directed ? g.csr.nnz : g.csr.nnz / 2; }
+int64_t edge_count(homln_t h, const GraphState &g) {
+    const int64_t e = csr_nnz(g.csr, h->stream);
+    return h->directed ? e : e / 2;
+}
 
 // Map a device-side error word to a status (and clear it).
 void check_device_error(homln_t h) {
@@ -331,12 +334,13 @@ GraphState &and_graph(homln_t h, uint64_t mask) {
     auto copy = [&](const Csr &src, Csr &dst) {
         dst.n = src.n;
         dst.nnz = src.nnz;
-        if (!dst.rowptr.alloc(&h->al, (size_t)h->n + 1) || !dst.col.alloc(&h->al, src.nnz > 0 ? src.nnz : 1))
+        dst.cap = src.cap;
+        if (!dst.rowptr.alloc(&h->al, (size_t)h->n + 1) || !dst.col.alloc(&h->al, src.cap > 0 ? src.cap : 1))
             fail(HOMLN_ENOMEM, "and graph");
         HCUDA(cudaMemcpyAsync(dst.rowptr.p, src.rowptr.p, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToDevice,
                               h->stream));
-        if (src.nnz > 0)
-            HCUDA(cudaMemcpyAsync(dst.col.p, src.col.p, sizeof(int32_t) * src.nnz, cudaMemcpyDeviceToDevice,
+        if (src.cap > 0)
+            HCUDA(cudaMemcpyAsync(dst.col.p, src.col.p, sizeof(int32_t) * src.cap, cudaMemcpyDeviceToDevice,
                                   h->stream));
     };
     if (ids.size() == 1) {

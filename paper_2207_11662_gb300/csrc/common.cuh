@@ -177,17 +177,23 @@ void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, Alloc *al, c
 // Result in keys/vals (the alternate buffers are scratch).
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit1, Alloc *al, cudaStream_t s);
 // Sort every CSR row's entries ascending, in place (segmented sort).
-void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cudaStream_t s);
+// cap: entries allocated in d_col (an upper bound on the longest row).
+void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, int64_t cap, Alloc *al, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Graph building (graph.cu)
 // ---------------------------------------------------------------------------
+// Rows are built without a host round trip: col is allocated with an upper bound (cap) on
+// the entries, and the exact count lives in rowptr[n] on the device until a caller needs it
+// on the host (csr_nnz, which synchronises once and caches it).
 struct Csr {
     int32_t n = 0;
-    int64_t nnz = 0;  // directed entries (2 x undirected edges)
+    int64_t cap = 0;           // entries allocated in col (>= the entries present)
+    mutable int64_t nnz = -1;  // entries present (2 x undirected edges); -1 until read
     DBuf<int64_t> rowptr;
     DBuf<int32_t> col;
 };
+int64_t csr_nnz(const Csr &g, cudaStream_t s);
 
 // Normalise an edge list (device int32 arrays) into a symmetric CSR with sorted rows.
 // directed: each edge goes into its source's row only (no symmetrisation).
@@ -254,7 +260,7 @@ struct BfsJob {
 void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
                  BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop);
 
-int msbfs_pick_words(int32_t n, int64_t nnz);
+int msbfs_pick_words(int32_t n);
 
 // ---------------------------------------------------------------------------
 // Finalize / selection / composition / accuracy (select.cu)

@@ -7,6 +7,8 @@
 // in every selected layer.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace homln {
 
 namespace {
@@ -228,7 +230,7 @@ unsigned grid_for(int64_t work, int threads = 256) {
     return (unsigned)(b > 65535 * 16 ? 65535 * 16 : b);
 }
 
-int64_t read_i64(const int64_t *d, cudaStream_t s) {
+int64_t read_i64_sync(const int64_t *d, cudaStream_t s) {
     int64_t v = 0;
     HCUDA(cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, s));
     HCUDA(cudaStreamSynchronize(s));
@@ -246,13 +248,15 @@ void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
     if (m == 0) {
         HCUDA(cudaMemsetAsync(out.rowptr.p, 0, sizeof(int64_t) * (n + 1), s));
         out.nnz = 0;
+        out.cap = 0;
         out.col.release();
         return;
     }
+    const int64_t raw_cap = (directed ? 1 : 2) * m;
     DBuf<int32_t> deg, raw, cnt;
     DBuf<int64_t> rp;
     DBuf<unsigned long long> cursor;
-    if (!deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cursor.alloc(al, n) || !raw.alloc(al, (directed ? 1 : 2) * m) ||
+    if (!deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cursor.alloc(al, n) || !raw.alloc(al, raw_cap) ||
         !cnt.alloc(al, n))
         fail(HOMLN_ENOMEM, "csr scratch");
     HCUDA(cudaMemsetAsync(deg.p, 0, sizeof(int32_t) * n, s));
@@ -262,16 +266,21 @@ void build_csr(int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
     HCUDA(cudaMemcpyAsync(cursor.p, rp.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
     if (directed) launch(k_scatter_edges<false>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
     else launch(k_scatter_edges<true>, grid_for(m), 256, 0, s, d_src, d_dst, m, n, cursor.p, raw.p);
-    sort_rows(n, rp.p, raw.p, al, s);
+    sort_rows(n, rp.p, raw.p, raw_cap, al, s);
     launch(k_row_unique<false>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
            (const int32_t *)raw.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr);
     scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
-    out.nnz = read_i64(out.rowptr.p + n, s);
-    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "csr col");
-    if (out.nnz > 0)
-        launch(k_row_unique<true>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
-               (const int32_t *)raw.p, (int32_t *)nullptr, (const int64_t *)out.rowptr.p, out.col.p);
+    out.cap = raw_cap;
+    out.nnz = -1;
+    if (!out.col.alloc(al, out.cap)) fail(HOMLN_ENOMEM, "csr col");
+    launch(k_row_unique<true>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
+           (const int32_t *)raw.p, (int32_t *)nullptr, (const int64_t *)out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
+}
+
+int64_t csr_nnz(const Csr &g, cudaStream_t s) {
+    if (g.nnz < 0) g.nnz = g.cap > 0 ? read_i64_sync(g.rowptr.p + g.n, s) : 0;
+    return g.nnz;
 }
 
 void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc *al, cudaStream_t s) {
@@ -282,13 +291,15 @@ void and_intersect(int32_t n, const std::vector<const Csr *> &layers, Csr &out, 
         L.col[i] = layers[i]->col.p;
     }
     out.n = n;
+    out.cap = layers[0]->cap;  // the intersection is no larger than any of its rows' layers
+    for (const Csr *c : layers) out.cap = std::min(out.cap, c->cap);
+    out.nnz = out.cap == 0 ? 0 : -1;
     DBuf<int32_t> cnt;
-    if (!out.rowptr.alloc(al, (size_t)n + 1) || !cnt.alloc(al, n)) fail(HOMLN_ENOMEM, "and scratch");
+    if (!out.rowptr.alloc(al, (size_t)n + 1) || !cnt.alloc(al, n) || !out.col.alloc(al, out.cap > 0 ? out.cap : 1))
+        fail(HOMLN_ENOMEM, "and scratch");
     launch(k_and_rows<false>, grid_for((int64_t)n * 32), 256, 0, s, n, L, cnt.p, nullptr, nullptr);
     scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
-    out.nnz = read_i64(out.rowptr.p + n, s);
-    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "and col");
-    if (out.nnz > 0)
+    if (out.cap > 0)
         launch(k_and_rows<true>, grid_for((int64_t)n * 32), 256, 0, s, n, L, nullptr, out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
 }
@@ -305,18 +316,20 @@ void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc
     DBuf<int64_t> rp;
     if (!out.rowptr.alloc(al, (size_t)n + 1) || !deg.alloc(al, n) || !rp.alloc(al, (size_t)n + 1) || !cnt.alloc(al, n))
         fail(HOMLN_ENOMEM, "or scratch");
+    int64_t total = 0;  // entries of the concatenated rows, at most
+    for (const Csr *c : layers) total += c->cap;
+    if (!cat.alloc(al, total > 0 ? total : 1)) fail(HOMLN_ENOMEM, "or rows");
     launch(k_sum_degrees, grid_for(n), 256, 0, s, n, L, deg.p);
     scan_exclusive_i32(deg.p, rp.p, n, al, s);
-    const int64_t total = read_i64(rp.p + n, s);
-    if (!cat.alloc(al, total > 0 ? total : 1)) fail(HOMLN_ENOMEM, "or rows");
     launch(k_concat_rows, grid_for((int64_t)n * 32), 256, 0, s, n, L, (const int64_t *)rp.p, cat.p);
-    sort_rows(n, rp.p, cat.p, al, s);
+    sort_rows(n, rp.p, cat.p, total, al, s);
     launch(k_row_unique<false>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
            (const int32_t *)cat.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr);
     scan_exclusive_i32(cnt.p, out.rowptr.p, n, al, s);
-    out.nnz = read_i64(out.rowptr.p + n, s);
-    if (!out.col.alloc(al, out.nnz > 0 ? out.nnz : 1)) fail(HOMLN_ENOMEM, "or col");
-    if (out.nnz > 0)
+    out.cap = total;
+    out.nnz = total == 0 ? 0 : -1;
+    if (!out.col.alloc(al, total > 0 ? total : 1)) fail(HOMLN_ENOMEM, "or col");
+    if (total > 0)
         launch(k_row_unique<true>, grid_for((int64_t)n * 32), 256, 0, s, n, (const int64_t *)rp.p,
                (const int32_t *)cat.p, (int32_t *)nullptr, (const int64_t *)out.rowptr.p, out.col.p);
     HCUDA(cudaGetLastError());
@@ -324,7 +337,7 @@ void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc
 
 void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s, bool directed) {
     int32_t n = g.n;
-    if (g.nnz == 0) return;
+    if (g.cap == 0) return;
     DBuf<int32_t> len;
     DBuf<int64_t> start, off;
     if (!len.alloc(al, n) || !start.alloc(al, n) || !off.alloc(al, (size_t)n + 1)) fail(HOMLN_ENOMEM, "edge list");
@@ -341,13 +354,14 @@ void relabel_apply(const Csr &g, const int32_t *perm, const int32_t *inv, Csr &o
     launch(k_perm_degrees, grid_for(n), 256, 0, s, n, g.rowptr.p, perm, newdeg.p);
     out.n = n;
     out.nnz = g.nnz;
-    if (!out.rowptr.alloc(al, (size_t)n + 1) || !out.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
+    out.cap = g.cap;
+    if (!out.rowptr.alloc(al, (size_t)n + 1) || !out.col.alloc(al, g.cap > 0 ? g.cap : 1))
         fail(HOMLN_ENOMEM, "relabel csr");
     scan_exclusive_i32(newdeg.p, out.rowptr.p, n, al, s);
-    if (g.nnz > 0) {
+    if (g.cap > 0) {
         launch(k_relabel_rows, grid_for((int64_t)n * 32), 256, 0, s, n, g.rowptr.p, g.col.p, perm, inv,
                out.rowptr.p, out.col.p);
-        sort_rows(n, out.rowptr.p, out.col.p, al, s);
+        sort_rows(n, out.rowptr.p, out.col.p, out.cap, al, s);
     }
     HCUDA(cudaGetLastError());
 }

@@ -96,10 +96,18 @@ struct Tile {
     bool atomic_fr;
 };
 
-// A vertex is "quiet" once its seen word has been full at the start of two levels: both
-// frontier buffers then hold zero for it and nothing can change it, so every later level
-// of the batch skips it after reading one byte.
-constexpr uint8_t QUIET = 2;
+// A vertex is "quiet" once its seen word is full: every later level of the batch skips it
+// after reading one byte, and its frontier words are no longer rewritten. What they still
+// hold are bits it found at earlier levels of the same batch, and a reader w (a neighbour,
+// or an out-neighbour when directed) already has each of them: a source s found at v on
+// level l reaches w by level l + 1, before w could read those words again at level l + 2.
+// So stale words never add a bit; only the second frontier buffer must start the batch at
+// zero (the first is written for every vertex at level 1). The quiet byte records the level
+// the vertex became full at (quiet_mark, never 0), so that a top-down level pushes its words
+// only while they are current: on the level right after.
+constexpr uint8_t QUIET = 1;  // quiet bytes >= QUIET mark full vertices
+
+__device__ __forceinline__ uint8_t quiet_mark(int level) { return (uint8_t)(QUIET + level % 255); }
 
 // Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices.
 constexpr int kChunkPasses = 4;
@@ -352,11 +360,10 @@ __device__ __forceinline__ void reset_next_slot(const Tile &a, uint32_t ps) {
 }
 
 // Record the new bits of v (already reduced to this lane's K words) and its counters.
-// full0: the vertex's seen word was already full when the level started (its new bits are 0).
 template <int W, bool STATS>
 __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writer, int64_t v, int q,
                                               const uint64_t (&s)[Geo<W>::K], const uint64_t (&nw)[Geo<W>::K],
-                                              uint64_t *nxt, int level, int64_t deg, bool full0, uint8_t qv,
+                                              uint64_t *nxt, int level, int64_t deg,
                                               PhaseCounters &c, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     bool any = false, full = true;
@@ -390,7 +397,7 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
             if (STATS) st[ST_BYTES] += 24;
         }
         if (!gfull) c.mu += (unsigned long long)deg;
-        if (full0) a.quiet[v] = qv + 1;
+        if (gfull) a.quiet[v] = quiet_mark(level);
         if (STATS) st[ST_VISITS] += 1;
     }
 }
@@ -398,9 +405,10 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
 // ---------------------------------------------------------------- phases
 
 // Level 0 and 1 of a batch: seen = own source bit (plus padding bits for a short
-// last batch); every source ORs its bit into its neighbours' accumulators.
+// last batch), the second frontier buffer fb = 0; every source ORs its bit into its
+// neighbours' accumulators.
 template <int W, bool STATS>
-__device__ void phase_start_batch(const Tile &a, int32_t s0, int32_t ns, unsigned long long *st) {
+__device__ void phase_start_batch(const Tile &a, uint64_t *fb, int32_t s0, int32_t ns, unsigned long long *st) {
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
@@ -415,8 +423,9 @@ __device__ void phase_start_batch(const Tile &a, int32_t s0, int32_t ns, unsigne
             if ((b >> 6) == wi) x |= 1ull << (b & 63);
         }
         a.seen[i] = x;
+        fb[i] = 0;
         if (wi == 0) a.quiet[v] = 0;
-        if (STATS) st[ST_BYTES] += 8 + (wi == 0);
+        if (STATS) st[ST_BYTES] += 16 + (wi == 0);
     }
     const int64_t e0 = a.rowptr[s0], e1 = a.rowptr[s0 + ns];
     for (int64_t e = e0 + gtid; e < e1; e += nthreads) {
@@ -449,7 +458,6 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
         const bool act = v < a.n && qv < QUIET;
         uint64_t s[K], z[K], nw[K];
         int64_t deg = 0;
-        bool lane_full = true;
 #pragma unroll
         for (int k = 0; k < K; ++k) s[k] = z[k] = nw[k] = 0;
         if (act) {
@@ -460,7 +468,6 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
             for (int k = 0; k < K; ++k) {
                 nw[k] = z[k] & ~s[k];
                 nz |= z[k] != 0;
-                lane_full &= s[k] == ~0ull;
             }
             if (nz) {
                 uint64_t zero[K];
@@ -471,8 +478,7 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
             deg = a.rowptr[v + 1] - a.rowptr[v];
             if (STATS) st[ST_BYTES] += (nz ? 24 : 16) * K + (q == 0 ? 16 : 0);
         }
-        const bool full0 = !group_any<T>(!lane_full);
-        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, full0, qv, c, st);
+        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, c, st);
     }
     flush_counters(a, c, ps);
 }
@@ -503,7 +509,6 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 acc[k] = 0;
                 lane_need |= need[k] != 0;
             }
-            const bool full0 = __syncthreads_or(lane_need ? 1 : 0) == 0;
             const int64_t rb = a.prow[v], re = a.prow[v + 1];
             int64_t it = 0;
             if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
@@ -532,7 +537,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                         for (int k = 0; k < K; ++k) t[k] |= red[w][lane][k];
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = t[k] & need[k];
-                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
+                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, c, st);
             }
             __syncthreads();
         }
@@ -576,7 +581,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 for (int k = 0; k < K; ++k) acc[k] |= __shfl_xor_sync(0xffffffffu, acc[k], o);
 #pragma unroll
             for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
+            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, c, st);
         }
     }
     // --- group tier: T lanes per vertex. Warps take chunks of vertices from the team's work
@@ -614,9 +619,6 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                     rb = a.prow[v];
                     re = a.prow[v + 1];
                 }
-                // every lane must take part in the shuffle, so no short-circuit around it
-                const bool group_needs = group_any<T>(lane_need);
-                const bool full0 = act && !group_needs;
                 int64_t it = 0;
                 if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
                 if (STATS) {
@@ -628,7 +630,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 }
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, full0, qv, c, st);
+                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, c, st);
             }
         }
     }
@@ -638,12 +640,15 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
 // Top-down level: frontier vertices OR their words into the neighbours' accumulators
 // (quiet neighbours are full and are skipped).
 template <int W, bool STATS>
-__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint32_t ps, unsigned long long *st) {
+__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, int level, uint32_t ps,
+                           unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
     auto push_row = [&](int64_t v, int p, int S) {
-        if (a.quiet[v] >= QUIET) return;  // a quiet vertex has an all-zero frontier word
+        // a full vertex's frontier words are current only on the level after it became full
+        const uint8_t qv = a.quiet[v];
+        if (qv >= QUIET && qv != quiet_mark(level - 1)) return;
         uint64_t f[K];
         ldw<K>(cur + v * W + q * K, f);
         if (STATS) st[ST_BYTES] += 8 * K + 1;
@@ -688,7 +693,7 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint
 template <int W, bool STATS>
 __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamBarrier &tb, int32_t s0, int32_t ns,
                           uint32_t &ps, PhaseCounters &c, unsigned long long *st) {
-    phase_start_batch<W, STATS>(a, s0, ns, st);
+    phase_start_batch<W, STATS>(a, fb, s0, ns, st);
     if (!team_sync(tb)) return false;
     phase_finalize<W, STATS>(a, fa, 1, ps, c, st);
     ++ps;
@@ -701,7 +706,7 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
         if (newbits == 0) break;
         const bool push = (unsigned long long)a.push_alpha * mf < mu;
         if (push) {
-            phase_push<W, STATS>(a, cur, ps, st);
+            phase_push<W, STATS>(a, cur, level, ps, st);
             if (!team_sync(tb)) return false;
             phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
         } else {
@@ -850,10 +855,10 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.atomic_fr = false;
     uint64_t *cur = cur_is_a ? fa : fb, *nxt = cur_is_a ? fb : fa;
     switch (kind) {
-    case PH_START: phase_start_batch<W, STATS>(a, s0, ns, st); break;
+    case PH_START: phase_start_batch<W, STATS>(a, fb, s0, ns, st); break;
     case PH_FINALIZE: phase_finalize<W, STATS>(a, nxt, level, ps, c, st); break;
     case PH_PULL: phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st); break;
-    default: phase_push<W, STATS>(a, cur, ps, st); break;
+    default: phase_push<W, STATS>(a, cur, level, ps, st); break;
     }
     if (STATS && A.stats) {
         if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -928,8 +933,7 @@ constexpr double kStateCap = 2.0e9;
 
 }  // namespace
 
-int msbfs_pick_words(int32_t n, int64_t nnz) {
-    (void)nnz;
+int msbfs_pick_words(int32_t n) {
     int W = 32;
     while (W > 1 && 4.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
     while (W > 1 && (int64_t)64 * (W / 2) >= n) W >>= 1;  // no wider than the node count needs
@@ -940,11 +944,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
                  BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
     if (jobs.empty()) return;
     int32_t maxn = 0;
-    int64_t maxnnz = 0;
-    for (const BfsJob &j : jobs) {
-        maxn = std::max(maxn, j.g->csr.n);
-        maxnnz = std::max(maxnnz, j.g->csr.nnz);
-    }
+    for (const BfsJob &j : jobs) maxn = std::max(maxn, j.g->csr.n);
     if (maxn <= 0) return;
     const int threads = t.threads > 0 ? t.threads : 512;
     if (threads % 32 != 0 || threads > 512 || threads < 64) fail(HOMLN_EINVAL, "threads must be 64..512, multiple of 32");
@@ -954,7 +954,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     // Defaults, measured on GB300: 8 words per node (512 sources per tile), 12 teams.
     // The plain schedule (one team, the host driving every level) takes the widest tile the
     // budget allows, which needs the fewest launches and host round trips.
-    int W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn, maxnnz) : std::min(8, msbfs_pick_words(maxn, maxnnz));
+    int W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn) : std::min(8, msbfs_pick_words(maxn));
     int nteams = 1;
     if (!plain) {
         if (t.teams > 0) {
@@ -1112,11 +1112,12 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
 static void copy_csr(const Csr &g, Csr &out, Alloc *al, cudaStream_t s) {
     out.n = g.n;
     out.nnz = g.nnz;
-    if (!out.rowptr.alloc(al, (size_t)g.n + 1) || !out.col.alloc(al, g.nnz > 0 ? g.nnz : 1))
+    out.cap = g.cap;
+    if (!out.rowptr.alloc(al, (size_t)g.n + 1) || !out.col.alloc(al, g.cap > 0 ? g.cap : 1))
         fail(HOMLN_ENOMEM, "bfs graph");
     HCUDA(cudaMemcpyAsync(out.rowptr.p, g.rowptr.p, sizeof(int64_t) * (g.n + 1), cudaMemcpyDeviceToDevice, s));
-    if (g.nnz > 0)
-        HCUDA(cudaMemcpyAsync(out.col.p, g.col.p, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToDevice, s));
+    if (g.cap > 0)
+        HCUDA(cudaMemcpyAsync(out.col.p, g.col.p, sizeof(int32_t) * g.cap, cudaMemcpyDeviceToDevice, s));
 }
 
 void bfs_prepare(const Csr &g, const Csr *g_in, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s) {

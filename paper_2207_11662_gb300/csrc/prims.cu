@@ -254,8 +254,8 @@ void rs_pass(const uint64_t *ka, const uint32_t *va, uint64_t *kb, uint32_t *vb,
 // Segmented sort of CSR rows (each row ascending, in place).
 // Rows of <= 32 entries: one warp, a bitonic network in registers. Rows of
 // 33 .. kRowSortSmem entries: one block, a bitonic network in shared memory.
-// Longer rows (rare: hubs of very large graphs) are collected and sorted one by
-// one with the radix sort.
+// Longer rows (rare: hubs of very large graphs): one block, shared-memory chunks
+// merged pairwise through a scratch copy. No host round trip.
 // ---------------------------------------------------------------------------
 constexpr int kRowSortSmem = 8192;
 
@@ -297,6 +297,32 @@ __global__ void k_sort_rows_small(int32_t n, const int64_t *__restrict__ rp, int
     }
 }
 
+// Bitonic sort of col[b, b + len) (len <= kRowSortSmem) in shared memory by one block.
+__device__ void block_sort_chunk(int32_t *__restrict__ sh, int32_t *__restrict__ col, int64_t b, int len) {
+    int P = 64;
+    while (P < len) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? col[b + i] : INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t x = sh[i], y = sh[l];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        sh[i] = y;
+                        sh[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) col[b + i] = sh[i];
+    __syncthreads();
+}
+
 // One block per listed row of 33 .. kRowSortSmem entries.
 __global__ void __launch_bounds__(256) k_sort_rows_mid(const int64_t *__restrict__ rp, int32_t *__restrict__ col,
                                                        const int32_t *__restrict__ mid, const int32_t *__restrict__ nlist) {
@@ -304,40 +330,50 @@ __global__ void __launch_bounds__(256) k_sort_rows_mid(const int64_t *__restrict
     const int32_t count = nlist[0];
     for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
         const int32_t r = mid[li];
-        const int64_t b = rp[r], d = rp[r + 1] - b;
-        int P = 64;
-        while (P < d) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < d ? col[b + i] : INT32_MAX;
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    const int l = i ^ j;
-                    if (l > i) {
-                        const int32_t x = sh[i], y = sh[l];
-                        const bool up = (i & k) == 0;
-                        if ((x > y) == up) {
-                            sh[i] = y;
-                            sh[l] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = threadIdx.x; i < d; i += blockDim.x) col[b + i] = sh[i];
-        __syncthreads();
+        block_sort_chunk(sh, col, rp[r], (int)(rp[r + 1] - rp[r]));
     }
 }
 
-__global__ void k_i32_to_u64(int64_t cnt, const int32_t *__restrict__ a, uint64_t *__restrict__ k) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        k[i] = (uint64_t)(uint32_t)a[i];
-}
-
-__global__ void k_u64_to_i32(int64_t cnt, const uint64_t *__restrict__ k, int32_t *__restrict__ a) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        a[i] = (int32_t)k[i];
+// One block per listed row longer than kRowSortSmem entries: sort chunks of kRowSortSmem in
+// shared memory, then merge runs pairwise (width kRowSortSmem, doubling) between the row and
+// its place in tmp[]. Each thread merges an equal share of a run pair's output, its start
+// found by a binary search along the merge path; equal keys come from the left run first.
+__global__ void __launch_bounds__(256) k_sort_rows_big(const int64_t *__restrict__ rp, int32_t *__restrict__ col,
+                                                       int32_t *__restrict__ tmp, const int32_t *__restrict__ big,
+                                                       const int32_t *__restrict__ nlist) {
+    __shared__ int32_t sh[kRowSortSmem];
+    const int32_t count = nlist[1];
+    for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
+        const int32_t r = big[li];
+        const int64_t b = rp[r], d = rp[r + 1] - b;
+        for (int64_t c0 = 0; c0 < d; c0 += kRowSortSmem)
+            block_sort_chunk(sh, col, b + c0, (int)(d - c0 < kRowSortSmem ? d - c0 : kRowSortSmem));
+        int32_t *src = col + b, *dst = tmp + b;
+        for (int64_t w = kRowSortSmem; w < d; w <<= 1) {
+            for (int64_t a0 = 0; a0 < d; a0 += 2 * w) {
+                const int64_t m1 = a0 + w < d ? a0 + w : d, e = a0 + 2 * w < d ? a0 + 2 * w : d;
+                const int32_t *A = src + a0, *B = src + m1;
+                const int64_t la = m1 - a0, lb = e - m1, total = e - a0;
+                const int64_t share = (total + blockDim.x - 1) / blockDim.x;
+                const int64_t k0 = min((int64_t)threadIdx.x * share, total), k1 = min(k0 + share, total);
+                int64_t lo = k0 - lb > 0 ? k0 - lb : 0, hi = k0 < la ? k0 : la;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (A[mid] <= B[k0 - mid - 1]) lo = mid + 1; else hi = mid;
+                }
+                int64_t i = lo, j = k0 - lo;
+                for (int64_t k = k0; k < k1; ++k) {
+                    if (j >= lb || (i < la && A[i] <= B[j])) dst[a0 + k] = A[i++];
+                    else dst[a0 + k] = B[j++];
+                }
+            }
+            __syncthreads();
+            int32_t *x = src; src = dst; dst = x;
+        }
+        if (src != col + b)
+            for (int64_t i = threadIdx.x; i < d; i += blockDim.x) col[b + i] = src[i];
+        __syncthreads();
+    }
 }
 
 unsigned grid_of(int64_t work, int threads) {
@@ -390,10 +426,12 @@ void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bit0, int bit
     }
 }
 
-void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cudaStream_t s) {
-    if (n <= 0) return;
-    DBuf<int32_t> mid, big, nlist;
-    if (!mid.alloc(al, n) || !big.alloc(al, n) || !nlist.alloc(al, 2)) fail(HOMLN_ENOMEM, "row sort scratch");
+void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, int64_t cap, Alloc *al, cudaStream_t s) {
+    if (n <= 0 || cap <= 1) return;
+    const bool may_be_big = cap > kRowSortSmem;  // a row cannot be longer than all entries together
+    DBuf<int32_t> mid, big, nlist, tmp;
+    if (!mid.alloc(al, n) || !big.alloc(al, n) || !nlist.alloc(al, 2) || (may_be_big && !tmp.alloc(al, cap)))
+        fail(HOMLN_ENOMEM, "row sort scratch");
     HCUDA(cudaMemsetAsync(nlist.p, 0, 2 * sizeof(int32_t), s));
     launch(k_sort_rows_small, grid_of((int64_t)n * 32, 256), 256, 0, s, n, d_rowptr, d_col, mid.p, big.p, nlist.p);
     int dev = 0, nsm = 0;
@@ -401,24 +439,9 @@ void sort_rows(int32_t n, const int64_t *d_rowptr, int32_t *d_col, Alloc *al, cu
     HCUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     launch(k_sort_rows_mid, (unsigned)(nsm * 4), 256, 0, s, (const int64_t *)d_rowptr, d_col, (const int32_t *)mid.p,
            (const int32_t *)nlist.p);
-    int32_t h_nbig = 0;
-    HCUDA(cudaMemcpyAsync(&h_nbig, nlist.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    HCUDA(cudaStreamSynchronize(s));
-    if (h_nbig == 0) return;
-    std::vector<int32_t> rows(h_nbig);
-    std::vector<int64_t> bounds(2);
-    HCUDA(cudaMemcpyAsync(rows.data(), big.p, sizeof(int32_t) * h_nbig, cudaMemcpyDeviceToHost, s));
-    HCUDA(cudaStreamSynchronize(s));
-    for (int32_t r : rows) {
-        HCUDA(cudaMemcpyAsync(bounds.data(), d_rowptr + r, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        HCUDA(cudaStreamSynchronize(s));
-        const int64_t b = bounds[0], d = bounds[1] - bounds[0];
-        DBuf<uint64_t> keys;
-        if (!keys.alloc(al, d)) fail(HOMLN_ENOMEM, "row sort keys");
-        launch(k_i32_to_u64, grid_of(d, 256), 256, 0, s, d, (const int32_t *)(d_col + b), keys.p);
-        radix_sort_u64(keys.p, nullptr, d, 0, 32, al, s);
-        launch(k_u64_to_i32, grid_of(d, 256), 256, 0, s, d, (const uint64_t *)keys.p, d_col + b);
-    }
+    if (may_be_big)
+        launch(k_sort_rows_big, (unsigned)nsm, 256, 0, s, (const int64_t *)d_rowptr, d_col, tmp.p,
+               (const int32_t *)big.p, (const int32_t *)nlist.p);
     HCUDA(cudaGetLastError());
 }
 
