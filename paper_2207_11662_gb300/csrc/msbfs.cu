@@ -52,6 +52,7 @@ struct TeamArgs {
     int64_t maxn;               // per-team state stride in vertices
     uint64_t *state;            // [4 arrays][nteams][maxn * W]: seen, frontier A, frontier B, accumulator
     uint8_t *quiet;             // [nteams][maxn]
+    uint8_t *fresh;             // [nteams][maxn]
     unsigned long long *ctr;    // [nteams][16]: 3 counter slots x {new bits, frontier edges, unfinished edges}
     uint32_t *bar;              // [nteams][32]: count, generation, ..., [8] current tile, [9] members
     uint32_t *sm_slots;         // [number of SMs]: blocks registered on each SM so far
@@ -84,6 +85,7 @@ struct Tile {
     uint64_t *seen;
     uint64_t *acc;
     uint8_t *quiet;
+    uint8_t *fresh;
     uint64_t *F;
     uint32_t *R;
     unsigned long long *ctr;
@@ -96,18 +98,17 @@ struct Tile {
     bool atomic_fr;
 };
 
+// Frontier words are written only by the lanes of a vertex that found new bits; otherwise
+// they keep bits the vertex found at an earlier level of the same batch. Such stale bits
+// never add a bit: a reader w (a neighbour, or an out-neighbour when directed) of v already
+// has each of them, since a source found at v on level l reaches w by level l + 1, before w
+// reads that buffer again at level l + 2. Both frontier buffers start a batch at zero.
 // A vertex is "quiet" once its seen word is full: every later level of the batch skips it
-// after reading one byte, and its frontier words are no longer rewritten. What they still
-// hold are bits it found at earlier levels of the same batch, and a reader w (a neighbour,
-// or an out-neighbour when directed) already has each of them: a source s found at v on
-// level l reaches w by level l + 1, before w could read those words again at level l + 2.
-// So stale words never add a bit; only the second frontier buffer must start the batch at
-// zero (the first is written for every vertex at level 1). The quiet byte records the level
-// the vertex became full at (quiet_mark, never 0), so that a top-down level pushes its words
-// only while they are current: on the level right after.
-constexpr uint8_t QUIET = 1;  // quiet bytes >= QUIET mark full vertices
+// after reading one byte. fresh[v] marks the last level at which v found new bits, so that a
+// top-down level pushes only the words written on the level before.
+constexpr uint8_t QUIET = 1;  // quiet byte of a full vertex
 
-__device__ __forceinline__ uint8_t quiet_mark(int level) { return (uint8_t)(QUIET + level % 255); }
+__device__ __forceinline__ uint8_t level_mark(int level) { return (uint8_t)(1 + level % 255); }
 
 // Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices.
 constexpr int kChunkPasses = 4;
@@ -376,10 +377,10 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
         full &= ns[k] == ~0ull;
         cnt += __popcll(nw[k]);
     }
-    if (act && writer) {
-        if (any) stw<K>(a.seen + v * W + q * K, ns);
+    if (act && writer && any) {
+        stw<K>(a.seen + v * W + q * K, ns);
         stw<K>(nxt + v * W + q * K, nw);
-        if (STATS) st[ST_BYTES] += (any ? 16 : 8) * K;
+        if (STATS) st[ST_BYTES] += 16 * K;
     }
     cnt = group_sum<T>(cnt);
     const bool gfull = !group_any<T>(!full);
@@ -394,10 +395,11 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
             }
             c.newbits += cnt;
             c.mf += (unsigned long long)deg;
-            if (STATS) st[ST_BYTES] += 24;
+            a.fresh[v] = level_mark(level);
+            if (STATS) st[ST_BYTES] += 25;
         }
         if (!gfull) c.mu += (unsigned long long)deg;
-        if (gfull) a.quiet[v] = quiet_mark(level);
+        if (gfull) a.quiet[v] = QUIET;
         if (STATS) st[ST_VISITS] += 1;
     }
 }
@@ -405,10 +407,11 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
 // ---------------------------------------------------------------- phases
 
 // Level 0 and 1 of a batch: seen = own source bit (plus padding bits for a short
-// last batch), the second frontier buffer fb = 0; every source ORs its bit into its
-// neighbours' accumulators.
+// last batch), both frontier buffers 0; every source ORs its bit into its neighbours'
+// accumulators.
 template <int W, bool STATS>
-__device__ void phase_start_batch(const Tile &a, uint64_t *fb, int32_t s0, int32_t ns, unsigned long long *st) {
+__device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int32_t s0, int32_t ns,
+                                  unsigned long long *st) {
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
@@ -423,9 +426,13 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *fb, int32_t s0, int32
             if ((b >> 6) == wi) x |= 1ull << (b & 63);
         }
         a.seen[i] = x;
+        fa[i] = 0;
         fb[i] = 0;
-        if (wi == 0) a.quiet[v] = 0;
-        if (STATS) st[ST_BYTES] += 16 + (wi == 0);
+        if (wi == 0) {
+            a.quiet[v] = 0;
+            a.fresh[v] = 0;
+        }
+        if (STATS) st[ST_BYTES] += 24 + 2 * (wi == 0);
     }
     const int64_t e0 = a.rowptr[s0], e1 = a.rowptr[s0 + ns];
     for (int64_t e = e0 + gtid; e < e1; e += nthreads) {
@@ -460,23 +467,26 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
         int64_t deg = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) s[k] = z[k] = nw[k] = 0;
+        bool nz = false;
         if (act) {
             ldw<K>(a.acc + v * W + q * K, z);
-            ldw<K>(a.seen + v * W + q * K, s);
-            bool nz = false;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                nw[k] = z[k] & ~s[k];
-                nz |= z[k] != 0;
-            }
+            for (int k = 0; k < K; ++k) nz |= z[k] != 0;
+            deg = a.rowptr[v + 1] - a.rowptr[v];
+            if (STATS) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
+        }
+        // a vertex nobody pushed to has no new bits (and, not being quiet, is not full)
+        if (group_any<T>(nz)) {
+            ldw<K>(a.seen + v * W + q * K, s);
+#pragma unroll
+            for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
             if (nz) {
                 uint64_t zero[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) zero[k] = 0;
                 stw<K>(a.acc + v * W + q * K, zero);
             }
-            deg = a.rowptr[v + 1] - a.rowptr[v];
-            if (STATS) st[ST_BYTES] += (nz ? 24 : 16) * K + (q == 0 ? 16 : 0);
+            if (STATS) st[ST_BYTES] += (nz ? 16 : 8) * K;
         }
         commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, c, st);
     }
@@ -646,9 +656,7 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, int 
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
     auto push_row = [&](int64_t v, int p, int S) {
-        // a full vertex's frontier words are current only on the level after it became full
-        const uint8_t qv = a.quiet[v];
-        if (qv >= QUIET && qv != quiet_mark(level - 1)) return;
+        if (a.fresh[v] != level_mark(level - 1)) return;  // no new bits on the previous level
         uint64_t f[K];
         ldw<K>(cur + v * W + q * K, f);
         if (STATS) st[ST_BYTES] += 8 * K + 1;
@@ -693,7 +701,7 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, int 
 template <int W, bool STATS>
 __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamBarrier &tb, int32_t s0, int32_t ns,
                           uint32_t &ps, PhaseCounters &c, unsigned long long *st) {
-    phase_start_batch<W, STATS>(a, fb, s0, ns, st);
+    phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st);
     if (!team_sync(tb)) return false;
     phase_finalize<W, STATS>(a, fa, 1, ps, c, st);
     ++ps;
@@ -760,6 +768,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
     uint64_t *fb = A.state + 2 * arr + team * stride;
     uint64_t *acc = A.state + 3 * arr + team * stride;
     uint8_t *quiet = A.quiet + (size_t)team * A.maxn;
+    uint8_t *fresh = A.fresh + (size_t)team * A.maxn;
     unsigned long long *ctr = A.ctr + (size_t)team * 16;
     volatile int32_t *tile_slot = reinterpret_cast<volatile int32_t *>(tbar + 8);
     uint32_t ps = 0;
@@ -783,6 +792,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         a.seen = seen;
         a.acc = acc;
         a.quiet = quiet;
+        a.fresh = fresh;
         a.F = g.F;
         a.R = g.R;
         a.ctr = ctr;
@@ -840,6 +850,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.seen = A.state;
     a.acc = A.state + 3 * arr;
     a.quiet = A.quiet;
+    a.fresh = A.fresh;
     a.F = g.F;
     a.R = g.R;
     a.ctr = A.ctr;
@@ -855,7 +866,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.atomic_fr = false;
     uint64_t *cur = cur_is_a ? fa : fb, *nxt = cur_is_a ? fb : fa;
     switch (kind) {
-    case PH_START: phase_start_batch<W, STATS>(a, fb, s0, ns, st); break;
+    case PH_START: phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st); break;
     case PH_FINALIZE: phase_finalize<W, STATS>(a, nxt, level, ps, c, st); break;
     case PH_PULL: phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st); break;
     default: phase_push<W, STATS>(a, cur, level, ps, st); break;
@@ -1020,7 +1031,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     DBuf<int32_t> queue;
     DBuf<GraphDesc> d_desc;
     const size_t bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
-    if (!state.alloc(al, 4 * words) || !quiet.alloc(al, (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
+    if (!state.alloc(al, 4 * words) || !quiet.alloc(al, 2 * (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
         !barmem.alloc(al, bar_words) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
         fail(HOMLN_ENOMEM, "bfs state");
     if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
@@ -1040,6 +1051,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     A.maxn = maxn;
     A.state = state.p;
     A.quiet = quiet.p;
+    A.fresh = quiet.p + (size_t)maxn * nteams;
     A.ctr = ctr.p;
     A.bar = barmem.p;
     A.grid_bar = barmem.p + 32 * (size_t)nteams;
