@@ -91,6 +91,9 @@ struct Selection {
     int32_t count = 0;
 };
 
+// A selection rule as a cache key: mode, percent (TOPK_PERCENT) and k (TOPK_COUNT).
+using SelKey = std::tuple<int32_t, double, int64_t>;
+
 // Partial results of one analysed graph (a layer or an AND aggregate).
 struct GraphState {
     Csr csr;     // rows = out-edges (all edges if undirected)
@@ -101,7 +104,7 @@ struct GraphState {
     DBuf<double> cc;
     DBuf<uint64_t> sumdist;
     DBuf<int32_t> deg;
-    std::map<std::tuple<int32_t, double, int64_t>, std::unique_ptr<Selection>> selections;
+    std::map<SelKey, std::unique_ptr<Selection>> selections;
     BfsGraph bfs;          // the graph as the BFS reads it (built once, kept by homln_invalidate)
     bool bfs_ready = false;
 };
@@ -110,8 +113,31 @@ struct GraphState {
 
 using namespace homln;
 
+// Side streams ("lanes") of a handle: independent per-graph work of one call (the layers' CSR
+// builds, the BFS graphs' relabellings, the layers' CC-node selections) runs on them side by
+// side, forked from and joined back into the handle's stream with events. Declared first in
+// the handle, so they are destroyed after every buffer freed on them.
+struct Lanes {
+    static constexpr int kCount = 4;
+    cudaStream_t s[kCount] = {};
+    Alloc al[kCount];  // the handle's allocator, bound to each lane
+    cudaEvent_t done[kCount] = {};
+    cudaEvent_t fork = nullptr;
+    ~Lanes() {
+        for (int i = 0; i < kCount; ++i) {
+            if (s[i]) {
+                cudaStreamSynchronize(s[i]);
+                cudaStreamDestroy(s[i]);
+            }
+            if (done[i]) cudaEventDestroy(done[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
 struct homln_s {
-    Alloc al;  // declared first: destroyed last, after every buffer that uses it
+    Lanes lanes;
+    Alloc al;  // declared before the buffers: destroyed after every buffer that uses it
     int device = 0;
     cudaStream_t stream = nullptr;
     int32_t n = 0, L = 0;
@@ -165,6 +191,36 @@ bool is_device_ptr(const void *p) {
 }
 
 void use_device(homln_t h) { HCUDA(cudaSetDevice(h->device)); }
+
+void lanes_open(homln_t h) {
+    Lanes &L = h->lanes;
+    for (int i = 0; i < Lanes::kCount; ++i) {
+        HCUDA(cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking));
+        HCUDA(cudaEventCreateWithFlags(&L.done[i], cudaEventDisableTiming));
+        L.al[i].a = h->al.a;
+        L.al[i].stream = L.s[i];
+    }
+    HCUDA(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
+}
+
+// The first `count` lanes wait for everything queued so far on the handle's stream.
+void lanes_fork(homln_t h, int count) {
+    Lanes &L = h->lanes;
+    count = std::min(count, Lanes::kCount);
+    if (count <= 0) return;
+    HCUDA(cudaEventRecord(L.fork, h->stream));
+    for (int i = 0; i < count; ++i) HCUDA(cudaStreamWaitEvent(L.s[i], L.fork, 0));
+}
+
+// The handle's stream waits for everything queued so far on the first `count` lanes.
+void lanes_join(homln_t h, int count) {
+    Lanes &L = h->lanes;
+    count = std::min(count, Lanes::kCount);
+    for (int i = 0; i < count; ++i) {
+        HCUDA(cudaEventRecord(L.done[i], L.s[i]));
+        HCUDA(cudaStreamWaitEvent(h->stream, L.done[i], 0));
+    }
+}
 
 // The CSR whose rows are the neighbours that reach a vertex: the in-edges of a directed graph.
 const Csr &in_csr(homln_t h, const GraphState &g) { return h->directed ? g.csr_in : g.csr; }
@@ -249,6 +305,7 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
     if (todo.empty()) return;
     std::vector<BfsJob> jobs;
     std::vector<homln_t> others;
+    std::vector<std::pair<homln_t, GraphState *>> prep;  // graphs whose BFS form must be (re)built
     for (const auto &it : todo) {
         homln_t o = it.first;
         GraphState *g = it.second;
@@ -256,14 +313,29 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
         if (!g->F.alloc(&o->al, n) || !g->R.alloc(&o->al, n) || !g->cc.alloc(&o->al, n) ||
             !g->sumdist.alloc(&o->al, n) || !g->deg.alloc(&o->al, n))
             fail(HOMLN_ENOMEM, "closeness outputs");
-        if (!g->bfs_ready || g->bfs.relabeled != (h->tuning.relabel != 0)) {
-            bfs_prepare(g->csr, o->directed ? &g->csr_in : nullptr, h->tuning.relabel != 0, g->bfs, &o->al, o->stream);
-            g->bfs_ready = true;
-        }
+        if (!g->bfs_ready || g->bfs.relabeled != (h->tuning.relabel != 0)) prep.push_back(it);
         jobs.push_back(BfsJob{&g->bfs, g->F.p, g->R.p});
         if (o != h && o->stream != h->stream && std::find(others.begin(), others.end(), o) == others.end())
             others.push_back(o);
     }
+    // the relabellings of h's graphs run on h's lanes side by side; other handles' on their streams
+    int nl = 0;
+    for (const auto &it : prep) nl += it.first == h;
+    lanes_fork(h, nl);
+    int k = 0;
+    for (const auto &it : prep) {
+        homln_t o = it.first;
+        GraphState *g = it.second;
+        const Csr *gin = o->directed ? &g->csr_in : nullptr;
+        if (o == h) {
+            const int j = k++ % Lanes::kCount;
+            bfs_prepare(g->csr, gin, h->tuning.relabel != 0, g->bfs, &h->lanes.al[j], h->lanes.s[j]);
+        } else {
+            bfs_prepare(g->csr, gin, h->tuning.relabel != 0, g->bfs, &o->al, o->stream);
+        }
+        g->bfs_ready = true;
+    }
+    lanes_join(h, nl);
     for (homln_t o : others) {  // h's stream waits for the CSRs and outputs queued on the other streams
         cudaEvent_t e;
         HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -361,9 +433,13 @@ GraphState &and_graph(homln_t h, uint64_t mask) {
 }
 
 // The graph's CC nodes under `sel`, computed once and cached (the closeness values never change).
+SelKey selection_key(const homln_select &sel) {
+    return std::make_tuple(sel.mode, sel.mode == HOMLN_TOPK_PERCENT ? sel.percent : 0.0,
+                           sel.mode == HOMLN_TOPK_COUNT ? sel.k : (int64_t)0);
+}
+
 Selection &selection_of(homln_t h, GraphState &g, const homln_select &sel) {
-    auto key = std::make_tuple(sel.mode, sel.mode == HOMLN_TOPK_PERCENT ? sel.percent : 0.0,
-                               sel.mode == HOMLN_TOPK_COUNT ? sel.k : (int64_t)0);
+    const SelKey key = selection_key(sel);
     auto it = g.selections.find(key);
     if (it != g.selections.end()) return *it->second;
     auto s = std::make_unique<Selection>();
@@ -373,6 +449,29 @@ Selection &selection_of(homln_t h, GraphState &g, const homln_select &sel) {
     Selection &ref = *s;
     g.selections.emplace(key, std::move(s));
     return ref;
+}
+
+// The CC nodes of several graphs under `sel`: those not cached yet are selected on the lanes
+// side by side (their outputs are allocated on the handle's stream first).
+void selections_of(homln_t h, const std::vector<GraphState *> &gs, const homln_select &sel) {
+    const SelKey key = selection_key(sel);
+    std::vector<std::pair<GraphState *, Selection *>> todo;
+    for (GraphState *g : gs) {
+        if (g->selections.count(key)) continue;
+        auto s = std::make_unique<Selection>();
+        if (!s->ranked.alloc(&h->al, h->n) || !s->bits.alloc(&h->al, ceil_div(h->n, 32)))
+            fail(HOMLN_ENOMEM, "selection");
+        todo.push_back({g, s.get()});
+        g->selections.emplace(key, std::move(s));
+    }
+    if (todo.empty()) return;
+    lanes_fork(h, (int)todo.size());
+    for (size_t i = 0; i < todo.size(); ++i) {
+        const int j = (int)(i % Lanes::kCount);
+        todo[i].second->count = select_nodes(h->n, todo[i].first->cc.p, sel, todo[i].second->ranked.p,
+                                             todo[i].second->bits.p, h->err.p, &h->lanes.al[j], h->lanes.s[j]);
+    }
+    lanes_join(h, (int)todo.size());
 }
 
 GraphState &or_graph(homln_t h, uint64_t mask) {
@@ -441,24 +540,35 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
     h->n = n_nodes;
     h->L = n_layers;
     h->directed = (flags & HOMLN_DIRECTED) != 0;
+    lanes_open(h.get());
     if (!h->err.alloc(&h->al, 1)) fail(HOMLN_ENOMEM, "error word");
     HCUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->stream));
+    // host edge lists are staged on the handle's stream; then the layers' CSRs are built on the lanes
+    std::vector<DBuf<int32_t>> staged(2 * (size_t)n_layers);
+    std::vector<const int32_t *> ps(n_layers), pd(n_layers);
     for (int i = 0; i < n_layers; ++i) {
-        auto g = std::make_unique<GraphState>();
         const int64_t m = edge_counts[i];
-        DBuf<int32_t> ds, dd;
-        const int32_t *ps = src[i], *pd = dst[i];
+        ps[i] = src[i];
+        pd[i] = dst[i];
         if (m > 0 && !(flags & HOMLN_PTR_DEVICE)) {
+            DBuf<int32_t> &ds = staged[2 * i], &dd = staged[2 * i + 1];
             if (!ds.alloc(&h->al, m) || !dd.alloc(&h->al, m)) fail(HOMLN_ENOMEM, "edge staging");
-            HCUDA(cudaMemcpyAsync(ds.p, ps, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
-            HCUDA(cudaMemcpyAsync(dd.p, pd, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
-            ps = ds.p;
-            pd = dd.p;
+            HCUDA(cudaMemcpyAsync(ds.p, ps[i], sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+            HCUDA(cudaMemcpyAsync(dd.p, pd[i], sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+            ps[i] = ds.p;
+            pd[i] = dd.p;
         }
-        build_csr(n_nodes, ps, pd, m, g->csr, h->err.p, &h->al, h->stream, h->directed);
-        if (h->directed) build_csr(n_nodes, pd, ps, m, g->csr_in, h->err.p, &h->al, h->stream, true);
-        h->layers.push_back(std::move(g));
+        h->layers.push_back(std::make_unique<GraphState>());
     }
+    lanes_fork(h.get(), n_layers);
+    for (int i = 0; i < n_layers; ++i) {
+        const int j = i % Lanes::kCount;
+        GraphState &g = *h->layers[i];
+        build_csr(n_nodes, ps[i], pd[i], edge_counts[i], g.csr, h->err.p, &h->lanes.al[j], h->lanes.s[j], h->directed);
+        if (h->directed)
+            build_csr(n_nodes, pd[i], ps[i], edge_counts[i], g.csr_in, h->err.p, &h->lanes.al[j], h->lanes.s[j], true);
+    }
+    lanes_join(h.get(), n_layers);
     check_device_error(h.get());
     *out = h.release();
     API_END
@@ -469,6 +579,8 @@ homln_status homln_destroy(homln_t h) {
     API_BEGIN
     cudaSetDevice(h->device);
     cudaStream_t s = h->stream;
+    // buffers owned by a lane are freed on it: after everything queued on the handle's stream
+    lanes_fork(h, Lanes::kCount);
     delete h;
     HCUDA(cudaStreamSynchronize(s));
     API_END
@@ -664,6 +776,9 @@ homln_status homln_compose(homln_t h, uint64_t layer_mask, int32_t heuristic, co
         // CC-node sets of the layers (cached per selection rule), intersected (naive), then CC1's refinement
         DBuf<uint32_t> common;
         if (!common.alloc(&h->al, nw)) fail(HOMLN_ENOMEM, "compose scratch");
+        std::vector<GraphState *> lg;
+        for (int i : ids) lg.push_back(h->layers[i].get());
+        selections_of(h, lg, *sel);
         for (size_t k = 0; k < ids.size(); ++k) {
             Selection &S = selection_of(h, *h->layers[ids[k]], *sel);
             if (k == 0)
