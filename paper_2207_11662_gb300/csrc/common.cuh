@@ -90,6 +90,43 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b, uint64_t limit_n
     return s_ok != 0;
 }
 
+// Which lanes' candidates v (ascending over the valid lanes [0, nv), distinct) occur in the
+// sorted row col[lo, hi) of distinct entries: the warp walks the row 32 entries at a time from
+// `lo`, one entry per lane, skips chunks below the candidates, stops at the first chunk above
+// them, and each lane looks its candidate up in a chunk by a binary search over the lanes
+// (shuffles). `lo` moves past the chunks that no later (larger) candidate can match, so a row
+// is walked once across ascending candidate chunks. Every lane of the warp must call it.
+__device__ __forceinline__ bool warp_row_has(const int32_t *__restrict__ col, int64_t &lo, int64_t hi, int32_t v,
+                                             int nv, int lane) {
+    const int32_t vmin = __shfl_sync(0xffffffffu, v, 0), vmax = __shfl_sync(0xffffffffu, v, nv - 1);
+    bool hit = false;
+    for (int64_t c = lo; c < hi; c += 32) {
+        const int64_t j = c + lane;
+        const int32_t w = j < hi ? __ldg(col + j) : INT32_MAX;
+        const int last = (int)(hi - 1 - c < 31 ? hi - 1 - c : 31);
+        const int32_t wmin = __shfl_sync(0xffffffffu, w, 0), wmax = __shfl_sync(0xffffffffu, w, last);
+        if (wmax < vmin) {
+            lo = c + 32;
+            continue;
+        }
+        if (wmin > vmax) break;
+        int a = 0, b = last;  // first entry >= v among lanes [0, last]
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (a + b) >> 1;
+            const int32_t wm = __shfl_sync(0xffffffffu, w, mid);
+            if (a < b) {
+                if (wm < v) a = mid + 1;
+                else b = mid;
+            }
+        }
+        hit |= __shfl_sync(0xffffffffu, w, a) == v;
+        if (wmax > vmax) break;  // the chunk reaches past the candidates: later ones start here
+        lo = c + 32;
+    }
+    return hit && lane < nv;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

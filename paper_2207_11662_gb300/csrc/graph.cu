@@ -93,25 +93,6 @@ struct LayerSet {
     int r;
 };
 
-// Which lanes' candidates v (ascending over the valid lanes [0, nv)) occur in the sorted row
-// col[lo, hi): the warp walks the row 32 entries at a time, skips chunks outside the
-// candidates' range, and compares every candidate with every entry of a chunk by shuffles.
-__device__ __forceinline__ bool warp_row_has(const int32_t *__restrict__ col, int64_t lo, int64_t hi, int32_t v,
-                                             int nv, int lane) {
-    const int32_t vmin = __shfl_sync(0xffffffffu, v, 0), vmax = __shfl_sync(0xffffffffu, v, nv - 1);
-    bool hit = false;
-    for (int64_t c = lo; c < hi; c += 32) {
-        const int64_t j = c + lane;
-        const int32_t w = j < hi ? __ldg(col + j) : INT32_MAX;
-        const int last = (int)(hi - 1 - c < 31 ? hi - 1 - c : 31);
-        const int32_t wmin = __shfl_sync(0xffffffffu, w, 0), wmax = __shfl_sync(0xffffffffu, w, last);
-        if (wmax < vmin) continue;
-        if (wmin > vmax) break;
-        for (int k = 0; k <= last; ++k) hit |= __shfl_sync(0xffffffffu, w, k) == v;
-    }
-    return hit && lane < nv;
-}
-
 // One warp per vertex: the lanes take the shortest of its rows 32 entries at a time and keep
 // the entries present in every other row; a ballot keeps them in order.
 template <bool WRITE>
@@ -129,6 +110,8 @@ __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, con
         }
         const int64_t b0 = L.rp[best][u];
         const int64_t o = WRITE ? out_rp[u] : 0;
+        int64_t cur[HOMLN_MAX_LAYERS];  // per other layer: where its row walk resumes
+        for (int i = 0; i < L.r; ++i) cur[i] = L.rp[i][u];
         int32_t c = 0;
         for (int64_t j0 = 0; j0 < best_len; j0 += 32) {
             const int64_t j = j0 + lane;
@@ -139,7 +122,7 @@ __global__ void k_and_rows(int32_t n, LayerSet L, int32_t *__restrict__ cnt, con
                 if (i == best) continue;
                 if (!__any_sync(0xffffffffu, all)) break;
                 // every lane takes part in the shuffles, so no short-circuit around the call
-                const bool has = warp_row_has(L.col[i], L.rp[i][u], L.rp[i][u + 1], v, nv, lane);
+                const bool has = warp_row_has(L.col[i], cur[i], L.rp[i][u + 1], v, nv, lane);
                 all = all && has;
             }
             const uint32_t m = __ballot_sync(0xffffffffu, all);

@@ -313,49 +313,50 @@ struct Cc1Layers {
     int r;
 };
 
-__device__ __forceinline__ bool in_row(const int32_t *__restrict__ col, int64_t lo, int64_t hi, int32_t x) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        int32_t c = col[mid];
-        if (c == x) return true;
-        if (c < x) lo = mid + 1; else hi = mid;
-    }
-    return false;
-}
-
 __device__ __forceinline__ bool bit_of(const uint32_t *b, int32_t v) { return (b[v >> 5] >> (v & 31)) & 1u; }
 
-// One warp per common CC node u: |AND_i C_i(u)| and |OR_i C_i(u)| with C_i(u) the central
-// neighbours of u in layer i; keep u iff the union is non-empty and AND >= theta * OR.
+// |AND_i C_i(u)| and |OR_i C_i(u)| with C_i(u) the central neighbours of u in layer i; keep u
+// iff the union is non-empty and AND >= theta * OR. One warp per common CC node u; the lanes
+// walk a row 32 entries at a time and test membership in the other rows with warp_row_has
+// (every lane takes part).
 __global__ void k_cc1_overlap(int32_t n, Cc1Layers L, const uint32_t *__restrict__ common, double theta,
                               uint32_t *__restrict__ out_bits) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = warp; u < n; u += nwarps) {
-        if (!bit_of(common, (int32_t)u)) continue;
-        unsigned long long inter = 0, uni = 0;
-        for (int i = 0; i < L.r; ++i) {
-            const int64_t b0 = L.rp[i][u], b1 = L.rp[i][u + 1];
-            for (int64_t j = b0 + lane; j < b1; j += 32) {
-                const int32_t v = L.col[i][j];
-                if (!bit_of(L.central[i], v)) continue;
-                bool earlier = false;  // already counted in the union through a lower layer
-                for (int k = 0; k < i && !earlier; ++k)
-                    earlier = bit_of(L.central[k], v) && in_row(L.col[k], L.rp[k][u], L.rp[k][u + 1], v);
-                if (!earlier) ++uni;
-                if (i == 0) {
-                    bool all = true;
-                    for (int k = 1; k < L.r && all; ++k)
-                        all = bit_of(L.central[k], v) && in_row(L.col[k], L.rp[k][u], L.rp[k][u + 1], v);
-                    if (all) ++inter;
+        if (!bit_of(common, (int32_t)u)) continue;  // uniform over the warp
+        {
+            unsigned long long inter = 0, uni = 0;
+            for (int i = 0; i < L.r; ++i) {
+                const int64_t b0 = L.rp[i][u], len = L.rp[i][u + 1] - b0;
+                int64_t cur[HOMLN_MAX_LAYERS];  // per other layer: where its row walk resumes
+                for (int k = 0; k < L.r; ++k) cur[k] = L.rp[k][u];
+                for (int64_t j0 = 0; j0 < len; j0 += 32) {
+                    const int nv = (int)(len - j0 < 32 ? len - j0 : 32);
+                    const int32_t v = lane < nv ? L.col[i][b0 + j0 + lane] : -1;
+                    const bool cen = lane < nv && bit_of(L.central[i], v);
+                    bool earlier = false;  // already counted in the union through a lower layer
+                    for (int k = 0; k < i; ++k) {
+                        const bool has = warp_row_has(L.col[k], cur[k], L.rp[k][u + 1], v, nv, lane);
+                        earlier = earlier || (has && bit_of(L.central[k], v));
+                    }
+                    if (cen && !earlier) ++uni;
+                    if (i == 0) {
+                        bool all = cen;
+                        for (int k = 1; k < L.r; ++k) {
+                            const bool has = warp_row_has(L.col[k], cur[k], L.rp[k][u + 1], v, nv, lane);
+                            all = all && has && bit_of(L.central[k], v);
+                        }
+                        if (all) ++inter;
+                    }
                 }
             }
+            inter = warp_sum(inter);
+            uni = warp_sum(uni);
+            if (lane == 0 && uni > 0 && (double)inter >= __dmul_rn(theta, (double)uni))
+                atomicOr(&out_bits[u >> 5], 1u << (u & 31));
         }
-        inter = warp_sum(inter);
-        uni = warp_sum(uni);
-        if (lane == 0 && uni > 0 && (double)inter >= __dmul_rn(theta, (double)uni))
-            atomicOr(&out_bits[u >> 5], 1u << (u & 31));
     }
 }
 
