@@ -50,9 +50,10 @@ struct TeamArgs {
     int32_t nteams;
     int32_t push_alpha;
     int64_t maxn;               // per-team state stride in vertices
-    uint64_t *state;            // [4 arrays][nteams][maxn * W]: seen, frontier A, frontier B, accumulator
+    uint64_t *state;            // [3 arrays][nteams][maxn * W]: seen, frontier A, frontier B
     uint8_t *quiet;             // [nteams][maxn]
     uint8_t *fresh;             // [nteams][maxn]
+    uint8_t *pushed;            // [nteams][maxn]
     unsigned long long *ctr;    // [nteams][16]: 3 counter slots x {new bits, frontier edges, unfinished edges}
     uint32_t *bar;              // [nteams][32]: count, generation, ..., [8] current tile, [9] members
     uint32_t *sm_slots;         // [number of SMs]: blocks registered on each SM so far
@@ -83,9 +84,9 @@ struct Tile {
     const int64_t *__restrict__ prow;    // in-edges (pull)
     const int32_t *__restrict__ pcol;
     uint64_t *seen;
-    uint64_t *acc;
     uint8_t *quiet;
     uint8_t *fresh;
+    uint8_t *pushed;  // a top-down level ORed words into the vertex's next frontier words
     uint64_t *F;
     uint32_t *R;
     unsigned long long *ctr;
@@ -406,9 +407,8 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
 
 // ---------------------------------------------------------------- phases
 
-// Level 0 and 1 of a batch: seen = own source bit (plus padding bits for a short
-// last batch), both frontier buffers 0; every source ORs its bit into its neighbours'
-// accumulators.
+// Level 0 of a batch: seen = own source bit (plus padding bits for a short last batch), both
+// frontier buffers 0, the per-vertex bytes 0.
 template <int W, bool STATS>
 __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int32_t s0, int32_t ns,
                                   unsigned long long *st) {
@@ -431,9 +431,18 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int
         if (wi == 0) {
             a.quiet[v] = 0;
             a.fresh[v] = 0;
+            a.pushed[v] = 0;
         }
-        if (STATS) st[ST_BYTES] += 24 + 2 * (wi == 0);
+        if (STATS) st[ST_BYTES] += 24 + 3 * (wi == 0);
     }
+}
+
+// Level 1, top-down: every source ORs its bit into its neighbours' words of the first frontier
+// buffer (zeroed by phase_start_batch before a team barrier).
+template <int W, bool STATS>
+__device__ void phase_start_push(const Tile &a, uint64_t *fa, int32_t s0, int32_t ns, unsigned long long *st) {
+    const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
+    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     const int64_t e0 = a.rowptr[s0], e1 = a.rowptr[s0 + ns];
     for (int64_t e = e0 + gtid; e < e1; e += nthreads) {
         int lo = 0, hi = ns;  // find the source row holding edge e
@@ -442,12 +451,14 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int
             if (a.rowptr[s0 + mid] <= e) lo = mid; else hi = mid;
         }
         const int32_t u = __ldg(a.col + e);
-        atomicOr(reinterpret_cast<unsigned long long *>(a.acc + (int64_t)u * W + (lo >> 6)), 1ull << (lo & 63));
-        if (STATS) { st[ST_BYTES] += 4 + 8; st[ST_PUSHED] += 1; st[ST_PUSHWORDS] += 1; }
+        atomicOr(reinterpret_cast<unsigned long long *>(fa + (int64_t)u * W + (lo >> 6)), 1ull << (lo & 63));
+        a.pushed[u] = 1;
+        if (STATS) { st[ST_BYTES] += 4 + 8 + 1; st[ST_PUSHED] += 1; st[ST_PUSHWORDS] += 1; }
     }
 }
 
-// Keep the accumulated bits not yet seen: they become the next frontier.
+// After a top-down level: of the words pushed into a vertex's next frontier words, the bits not
+// yet seen are its new bits (the rest, and what the words held before, are bits it has).
 template <int W, bool STATS>
 __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c,
                                unsigned long long *st) {
@@ -457,38 +468,33 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
     for (int64_t v = gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-        uint8_t qv = 0;
+        uint8_t qv = 0, pv = 0;
         if (v < a.n) {
             qv = a.quiet[v];
-            if (STATS && q == 0) st[ST_BYTES] += 1;
+            pv = a.pushed[v];
+            if (STATS && q == 0) st[ST_BYTES] += 2;
         }
         const bool act = v < a.n && qv < QUIET;
-        uint64_t s[K], z[K], nw[K];
+        uint64_t s[K], nw[K];
         int64_t deg = 0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) s[k] = z[k] = nw[k] = 0;
-        bool nz = false;
+        for (int k = 0; k < K; ++k) s[k] = nw[k] = 0;
         if (act) {
-            ldw<K>(a.acc + v * W + q * K, z);
-#pragma unroll
-            for (int k = 0; k < K; ++k) nz |= z[k] != 0;
             deg = a.rowptr[v + 1] - a.rowptr[v];
-            if (STATS) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
-        }
-        // a vertex nobody pushed to has no new bits (and, not being quiet, is not full)
-        if (group_any<T>(nz)) {
-            ldw<K>(a.seen + v * W + q * K, s);
+            if (STATS && q == 0) st[ST_BYTES] += 16;
+            // a vertex nobody pushed to has no new bits (and, not being quiet, is not full)
+            if (pv) {
+                uint64_t z[K];
+                ldw<K>(nxt + v * W + q * K, z);
+                ldw<K>(a.seen + v * W + q * K, s);
 #pragma unroll
-            for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
-            if (nz) {
-                uint64_t zero[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) zero[k] = 0;
-                stw<K>(a.acc + v * W + q * K, zero);
+                for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
+                if (STATS) st[ST_BYTES] += 16 * K;
             }
-            if (STATS) st[ST_BYTES] += (nz ? 16 : 8) * K;
         }
         commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, c, st);
+        // after the group's shuffles in commit_vertex: every lane of the group has read pv
+        if (act && pv && q == 0) a.pushed[v] = 0;
     }
     flush_counters(a, c, ps);
 }
@@ -650,7 +656,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
 // Top-down level: frontier vertices OR their words into the neighbours' accumulators
 // (quiet neighbours are full and are skipped).
 template <int W, bool STATS>
-__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, int level, uint32_t ps,
+__device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint64_t *nxt, int level, uint32_t ps,
                            unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
@@ -672,9 +678,11 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, int 
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (f[k]) {
-                    atomicOr(reinterpret_cast<unsigned long long *>(a.acc + u * W + q * K + k), f[k]);
+                    atomicOr(reinterpret_cast<unsigned long long *>(nxt + u * W + q * K + k), f[k]);
                     if (STATS) { st[ST_PUSHWORDS] += 1; st[ST_BYTES] += 8; }
                 }
+            a.pushed[u] = 1;
+            if (STATS) st[ST_BYTES] += 1;
         }
     };
     for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) push_row(v, threadIdx.x / T, blockDim.x / T);
@@ -703,6 +711,8 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
                           uint32_t &ps, PhaseCounters &c, unsigned long long *st) {
     phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st);
     if (!team_sync(tb)) return false;
+    phase_start_push<W, STATS>(a, fa, s0, ns, st);
+    if (!team_sync(tb)) return false;
     phase_finalize<W, STATS>(a, fa, 1, ps, c, st);
     ++ps;
     if (!team_sync(tb)) return false;
@@ -714,7 +724,7 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
         if (newbits == 0) break;
         const bool push = (unsigned long long)a.push_alpha * mf < mu;
         if (push) {
-            phase_push<W, STATS>(a, cur, level, ps, st);
+            phase_push<W, STATS>(a, cur, nxt, level, ps, st);
             if (!team_sync(tb)) return false;
             phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
         } else {
@@ -766,9 +776,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
     uint64_t *seen = A.state + 0 * arr + team * stride;
     uint64_t *fa = A.state + 1 * arr + team * stride;
     uint64_t *fb = A.state + 2 * arr + team * stride;
-    uint64_t *acc = A.state + 3 * arr + team * stride;
     uint8_t *quiet = A.quiet + (size_t)team * A.maxn;
     uint8_t *fresh = A.fresh + (size_t)team * A.maxn;
+    uint8_t *pushed = A.pushed + (size_t)team * A.maxn;
     unsigned long long *ctr = A.ctr + (size_t)team * 16;
     volatile int32_t *tile_slot = reinterpret_cast<volatile int32_t *>(tbar + 8);
     uint32_t ps = 0;
@@ -790,9 +800,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         a.prow = g.prow;
         a.pcol = g.pcol;
         a.seen = seen;
-        a.acc = acc;
         a.quiet = quiet;
         a.fresh = fresh;
+        a.pushed = pushed;
         a.F = g.F;
         a.R = g.R;
         a.ctr = ctr;
@@ -830,7 +840,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
 
 // One phase of one graph as an ordinary (non-cooperative) launch: the plain schedule, in
 // which the host drives the levels and kernel boundaries replace the team barrier.
-enum PhaseKind { PH_START = 0, PH_FINALIZE = 1, PH_PULL = 2, PH_PUSH = 3 };
+enum PhaseKind { PH_START = 0, PH_FINALIZE = 1, PH_PULL = 2, PH_PUSH = 3, PH_START_PUSH = 4 };
 
 template <int W, bool STATS>
 __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
@@ -848,9 +858,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     a.prow = g.prow;
     a.pcol = g.pcol;
     a.seen = A.state;
-    a.acc = A.state + 3 * arr;
     a.quiet = A.quiet;
     a.fresh = A.fresh;
+    a.pushed = A.pushed;
     a.F = g.F;
     a.R = g.R;
     a.ctr = A.ctr;
@@ -867,9 +877,10 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A,
     uint64_t *cur = cur_is_a ? fa : fb, *nxt = cur_is_a ? fb : fa;
     switch (kind) {
     case PH_START: phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st); break;
+    case PH_START_PUSH: phase_start_push<W, STATS>(a, fa, s0, ns, st); break;
     case PH_FINALIZE: phase_finalize<W, STATS>(a, nxt, level, ps, c, st); break;
     case PH_PULL: phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st); break;
-    default: phase_push<W, STATS>(a, cur, level, ps, st); break;
+    default: phase_push<W, STATS>(a, cur, nxt, level, ps, st); break;
     }
     if (STATS && A.stats) {
         if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -932,7 +943,7 @@ BfsKernel kernel_for(int W, bool stats) {
     }
 }
 
-// Widest tile: one team's state (4 arrays of n x W words) stays within this many bytes.
+// Widest tile: one team's state (3 arrays of n x W words) stays within this many bytes.
 constexpr double kWordsBudget = 104.0e6;
 // Default teams, measured on GB300 (W = 8, 304 blocks): 12 teams were best or within noise of
 // it on both the 50,000-node power-law workload (8 teams: 3% slower) and the 200,000-node BA
@@ -946,7 +957,7 @@ constexpr double kStateCap = 2.0e9;
 
 int msbfs_pick_words(int32_t n) {
     int W = 32;
-    while (W > 1 && 4.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
+    while (W > 1 && 3.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
     while (W > 1 && (int64_t)64 * (W / 2) >= n) W >>= 1;  // no wider than the node count needs
     return W;
 }
@@ -971,7 +982,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
         if (t.teams > 0) {
             nteams = t.teams;
         } else {
-            nteams = (int)std::floor(kStateCap / (4.0 * maxn * 8.0 * W));
+            nteams = (int)std::floor(kStateCap / (3.0 * maxn * 8.0 * W));
             nteams = std::max(1, std::min(kDefaultTeams, nteams));
             int64_t tiles = 0;  // no more teams than tiles
             for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
@@ -1031,11 +1042,10 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     DBuf<int32_t> queue;
     DBuf<GraphDesc> d_desc;
     const size_t bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
-    if (!state.alloc(al, 4 * words) || !quiet.alloc(al, 2 * (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
+    if (!state.alloc(al, 3 * words) || !quiet.alloc(al, 3 * (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
         !barmem.alloc(al, bar_words) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
         fail(HOMLN_ENOMEM, "bfs state");
     if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
-    HCUDA(cudaMemsetAsync(state.p + 3 * words, 0, words * sizeof(uint64_t), s));  // accumulators
     HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
     HCUDA(cudaMemsetAsync(barmem.p, 0, bar_words * sizeof(uint32_t), s));
     HCUDA(cudaMemsetAsync(queue.p, 0, sizeof(int32_t), s));
@@ -1052,6 +1062,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     A.state = state.p;
     A.quiet = quiet.p;
     A.fresh = quiet.p + (size_t)maxn * nteams;
+    A.pushed = quiet.p + 2 * (size_t)maxn * nteams;
     A.ctr = ctr.p;
     A.bar = barmem.p;
     A.grid_bar = barmem.p + 32 * (size_t)nteams;
@@ -1075,6 +1086,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
             for (int32_t b = 0; b < desc[gi].nbatches; ++b) {
                 const int32_t s0 = b * 64 * W, ns = std::min(64 * W, desc[gi].n - s0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START_PUSH, s0, ns, 0, ps, 0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, 1, ps, 0);
                 ++ps;
                 int32_t cur_a = 1;
