@@ -945,12 +945,12 @@ BfsKernel kernel_for(int W, bool stats) {
 
 // Widest tile: one team's state (3 arrays of n x W words) stays within this many bytes.
 constexpr double kWordsBudget = 104.0e6;
-// Default teams, measured on GB300 (W = 8, 304 blocks): 12 teams were best or within noise of
-// it on both the 50,000-node power-law workload (8 teams: 3% slower) and the 200,000-node BA
-// workload (2 teams: 24% slower, 24 teams: 4% slower). The frontier gathers of more teams
-// than fit L2 still hit L2 mostly, and smaller teams meet at their barriers sooner. The
-// state of all teams is capped at kStateCap bytes.
-constexpr int kDefaultTeams = 12;
+// Default teams, measured on GB300 (W = 8, 304 blocks): 16 teams were best or within noise of
+// it on both the 50,000-node power-law workload (8 teams: 5% slower, 12: 1%, 24: equal) and
+// the 200,000-node BA workload (8-16 equal, 2 teams: 24% slower). The frontier gathers of
+// more teams than fit L2 still hit L2 mostly, and smaller teams meet at their barriers
+// sooner. The state of all teams is capped at kStateCap bytes.
+constexpr int kDefaultTeams = 16;
 constexpr double kStateCap = 2.0e9;
 
 }  // namespace
@@ -973,7 +973,7 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
 
     const bool plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
-    // Defaults, measured on GB300: 8 words per node (512 sources per tile), 12 teams.
+    // Defaults, measured on GB300: 8 words per node (512 sources per tile), 16 teams.
     // The plain schedule (one team, the host driving every level) takes the widest tile the
     // budget allows, which needs the fewest launches and host round trips.
     int W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn) : std::min(8, msbfs_pick_words(maxn));
