@@ -571,10 +571,15 @@ def main():
         net, desc = make_workload(args.workload, 0)
         for _ in range(args.warmup):
             cpu_baseline(net, max(50, args.cpu_sample_sources // 10))
-        vals = [cpu_baseline(net, args.cpu_sample_sources, seed=2001 + k) for k in range(args.steps)]
+        vals, secs = [], []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            vals.append(cpu_baseline(net, args.cpu_sample_sources, seed=2001 + k))
+            secs.append(time.perf_counter() - t0)
         v = statistics.mean(x["value"] for x in vals)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GTEPS",
-                          "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": round(1000.0 * statistics.mean(secs), 3), "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                           "config": {"workload": desc},
                           "cpu_baseline": dict(vals[-1], value=round(v, 4)),
