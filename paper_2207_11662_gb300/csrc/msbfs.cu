@@ -233,7 +233,7 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b, uint64_t limit_n
 #define HOMLN_WARP_COORD 1
 #endif
 #ifndef HOMLN_WARP_TIER_ITERS
-#define HOMLN_WARP_TIER_ITERS 4
+#define HOMLN_WARP_TIER_ITERS 8
 #endif
 #ifndef HOMLN_BLOCK_TIER_ITERS
 #define HOMLN_BLOCK_TIER_ITERS 4
@@ -807,7 +807,9 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         a.R = g.R;
         a.ctr = ctr;
         a.n = g.n;
-        // hub tiers: rows of at least 4 iterations per slot go to a whole block / a whole warp
+        // hub tiers: rows of at least HOMLN_BLOCK_TIER_ITERS (4) iterations per slot of a block go
+        // to a whole block, the rest with at least HOMLN_WARP_TIER_ITERS (8) per slot of a warp to
+        // a whole warp (measured on GB300: warp threshold 8 beat 2, 4, 12, 16 and 32)
         a.hub_block_end =
             g.by_degree ? first_below(g.prow, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
         a.hub_warp_end = g.by_degree
