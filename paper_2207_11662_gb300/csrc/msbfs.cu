@@ -112,7 +112,13 @@ constexpr uint8_t QUIET = 1;  // quiet byte of a full vertex
 __device__ __forceinline__ uint8_t level_mark(int level) { return (uint8_t)(1 + level % 255); }
 
 // Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices.
-constexpr int kChunkPasses = 4;
+#ifndef HOMLN_CHUNK_PASSES
+#define HOMLN_CHUNK_PASSES 4
+#endif
+constexpr int kChunkPasses = HOMLN_CHUNK_PASSES;
+#ifndef HOMLN_WORDS_PER_LANE
+#define HOMLN_WORDS_PER_LANE 2
+#endif
 
 enum {
     ST_LEVELS, ST_PULL, ST_PUSH, ST_EDGES, ST_WORDS, ST_PUSHED, ST_BATCHES, ST_PUSHWORDS, ST_BYTES, ST_VISITS, ST_N
@@ -120,13 +126,19 @@ enum {
 
 template <int W>
 struct Geo {
-    static constexpr int K = W >= 2 ? 2 : 1;  // 64-bit words per lane
+    static constexpr int K = W >= HOMLN_WORDS_PER_LANE ? HOMLN_WORDS_PER_LANE : W;  // 64-bit words per lane
     static constexpr int T = W / K;           // lanes per vertex
 };
 
 template <int K>
 __device__ __forceinline__ void ldw(const uint64_t *p, uint64_t (&x)[K]) {
-    if constexpr (K == 2) {
+    if constexpr (K == 4) {
+        const ulonglong2 t0 = reinterpret_cast<const ulonglong2 *>(p)[0], t1 = reinterpret_cast<const ulonglong2 *>(p)[1];
+        x[0] = t0.x;
+        x[1] = t0.y;
+        x[2] = t1.x;
+        x[3] = t1.y;
+    } else if constexpr (K == 2) {
         ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
         x[0] = t.x;
         x[1] = t.y;
@@ -137,7 +149,10 @@ __device__ __forceinline__ void ldw(const uint64_t *p, uint64_t (&x)[K]) {
 
 template <int K>
 __device__ __forceinline__ void stw(uint64_t *p, const uint64_t (&x)[K]) {
-    if constexpr (K == 2) {
+    if constexpr (K == 4) {
+        reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(x[0], x[1]);
+        reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(x[2], x[3]);
+    } else if constexpr (K == 2) {
         *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x[0], x[1]);
     } else {
         *p = x[0];
@@ -510,7 +525,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
 
     // --- block tier: the largest hubs, all slots of the block share one row
     {
-        __shared__ uint64_t red[32][16][2];
+        __shared__ uint64_t red[32][16][Geo<W>::K];
         const int S = blockDim.x / T, p = threadIdx.x / T;
         for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) {
             const uint8_t qv = a.quiet[v];
