@@ -10,9 +10,9 @@
  *   (analysis step Psi, composition step Theta).
  *
  * Conventions used by every call
- *   - Graphs are undirected and unweighted. Node ids are int32 in [0, n).
- *     Self loops and repeated edges in the input are accepted and dropped
- *     (simple-graph semantics, Section 4).
+ *   - Graphs are unweighted and undirected (or directed with HOMLN_DIRECTED). Node
+ *     ids are int32 in [0, n). Self loops and repeated edges in the input are
+ *     accepted and dropped (simple-graph semantics, Section 4).
  *   - All GPU work runs on the CUDA stream given to homln_create, on the device
  *     that was current at homln_create.
  *   - Output pointers may be host memory (pageable or pinned) or device memory;
@@ -20,7 +20,11 @@
  *     output returns after the data is there (it synchronises the stream). A call
  *     whose outputs are all device memory only enqueues work and returns; errors
  *     raised by that work on the device surface at the next synchronising call or
- *     at homln_sync.
+ *     at homln_sync. Device-side waits are bounded (homln_tuning.wait_limit_ms):
+ *     a wait that runs out makes the kernel stop and the call report
+ *     HOMLN_ETIMEOUT. When a device-side error is reported, the handle drops its
+ *     cached results (as homln_invalidate does) and stays usable; after a failed
+ *     homln_batch_analyse, invalidate every handle of the batch.
  *   - Every call returns a homln_status. No C++ exception crosses this boundary.
  *     On error the outputs are left untouched unless stated otherwise, and
  *     homln_last_error() returns a message for the calling thread.
@@ -130,6 +134,11 @@ typedef struct homln_tuning {
     int32_t schedule;        /* 0 (default): one persistent launch over all (graph, batch) tiles;
                                 1: plain -- one ordinary launch per BFS phase, levels driven by the host
                                    (the comparison baseline; identical results) */
+    int32_t wait_limit_ms;   /* give-up time of every device-side wait of the BFS (team and grid
+                                barriers); the call then fails with HOMLN_ETIMEOUT (0 = 2000 ms) */
+    int32_t test_phantom_blocks; /* failure-detection tests only: every team barrier of the
+                                persistent BFS also waits for this many blocks that do not exist,
+                                so its wait runs out after wait_limit_ms (0 = off) */
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.
@@ -296,6 +305,24 @@ HOMLN_API homln_status homln_get_profile(homln_t h, homln_profile_t *out);
 HOMLN_API homln_status homln_reset_profile(homln_t h);
 /* Number of kernels this library has launched in the process so far. */
 HOMLN_API int64_t homln_kernel_launches(void);
+
+/* Checkpoint of the Psi step (Section 3 keeps each layer's analysis results for every later
+ * composition): the partial results of one graph -- which = layer id, -1 for the AND graph or
+ * -2 for the OR graph of layer_mask -- analysed first if needed.
+ *   farness[n] (uint64), reach[n] (uint32): as homln_layer_closeness; degree[n] (int32, may
+ *   be NULL): the degree used by CC1 (the in-degree when directed). Host or device memory.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+HOMLN_API homln_status homln_export_partials(homln_t h, int32_t which, uint64_t layer_mask, uint64_t *farness,
+                                             uint32_t *reach, int32_t *degree);
+
+/* Resume from a checkpoint: take farness/reach (host or device, n entries each) as the analysis
+ * of graph `which` (as in homln_export_partials) of this handle, which must hold the same layers
+ * they were computed on; closeness, sumDist and degrees are derived from them and the handle's
+ * CSRs, and later queries on that graph run no BFS. Cached selections of the graph are dropped.
+ * Errors: EINVAL; ERANGE (some (F, R) no BFS on n nodes can produce: R > n-1, F < R,
+ * F > R (n-1)) -- the graph's previous results are then kept; ENOMEM, ECUDA. */
+HOMLN_API homln_status homln_import_partials(homln_t h, int32_t which, uint64_t layer_mask, const uint64_t *farness,
+                                             const uint32_t *reach);
 
 /* Drop the cached Psi results (closeness, farness, selections) of every graph of the handle;
  * the CSRs and AND graphs stay. The next query recomputes them (used to re-measure). */

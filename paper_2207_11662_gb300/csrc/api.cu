@@ -236,6 +236,22 @@ int64_t edge_count(homln_t h, const GraphState &g) {
     return h->directed ? e : e / 2;
 }
 
+// Forget every cached analysis result (closeness, selections); CSRs and BFS graphs stay.
+void drop_results(homln_t h) {
+    auto drop = [](GraphState &g) {
+        g.analysed = false;
+        g.selections.clear();
+        g.F.release();
+        g.R.release();
+        g.cc.release();
+        g.sumdist.release();
+        g.deg.release();
+    };
+    for (auto &g : h->layers) drop(*g);
+    for (auto &kv : h->ands) drop(*kv.second);
+    for (auto &kv : h->ors) drop(*kv.second);
+}
+
 // Map a device-side error word to a status (and clear it).
 void check_device_error(homln_t h) {
     int32_t e = 0;
@@ -243,6 +259,7 @@ void check_device_error(homln_t h) {
     HCUDA(cudaStreamSynchronize(h->stream));
     if (e == DEV_OK) return;
     HCUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->stream));
+    drop_results(h);  // what the failed work left in the cached results is not trusted
     switch (e) {
     case DEV_BAD_ID: fail(HOMLN_EINVAL, "node id outside [0, n)");
     case DEV_TIMEOUT: fail(HOMLN_ETIMEOUT, "a bounded device wait gave up");
@@ -617,6 +634,11 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         bt.team_mix = t->team_mix ? 1 : 0;
         if (t->schedule < 0 || t->schedule > 1) fail(HOMLN_EINVAL, "schedule must be 0 or 1");
         bt.schedule = t->schedule;
+        if (t->wait_limit_ms < 0 || t->wait_limit_ms > 60000) fail(HOMLN_EINVAL, "wait_limit_ms must be in [0, 60000]");
+        if (t->wait_limit_ms) bt.wait_limit_ms = t->wait_limit_ms;
+        if (t->test_phantom_blocks < 0 || t->test_phantom_blocks > 1024)
+            fail(HOMLN_EINVAL, "test_phantom_blocks must be in [0, 1024]");
+        bt.phantom = t->test_phantom_blocks;
     }
     h->tuning = bt;
     API_END
@@ -731,6 +753,69 @@ homln_status homln_and_closeness(homln_t h, uint64_t layer_mask, uint64_t *farne
     GraphState &g = and_graph(h, layer_mask);
     analyse(h, g);
     write_closeness(h, g, farness, reach, cc);
+    API_END
+}
+
+namespace {
+GraphState &graph_of(homln_t h, int32_t which, uint64_t layer_mask) {
+    if (which < -2 || which >= h->L) fail(HOMLN_EINVAL, "which must be -2, -1 or a layer id");
+    return which >= 0 ? *h->layers[which] : which == -1 ? and_graph(h, layer_mask) : or_graph(h, layer_mask);
+}
+}  // namespace
+
+homln_status homln_export_partials(homln_t h, int32_t which, uint64_t layer_mask, uint64_t *farness, uint32_t *reach,
+                                   int32_t *degree) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!farness || !reach) fail(HOMLN_EINVAL, "farness and reach are required");
+    use_device(h);
+    GraphState &g = graph_of(h, which, layer_mask);
+    analyse(h, g);
+    bool host = put_out(h, farness, g.F.p, sizeof(uint64_t) * h->n);
+    host |= put_out(h, reach, g.R.p, sizeof(uint32_t) * h->n);
+    host |= put_out(h, degree, g.deg.p, sizeof(int32_t) * h->n);
+    if (host) check_device_error(h);
+    API_END
+}
+
+homln_status homln_import_partials(homln_t h, int32_t which, uint64_t layer_mask, const uint64_t *farness,
+                                   const uint32_t *reach) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!farness || !reach) fail(HOMLN_EINVAL, "farness and reach are required");
+    use_device(h);
+    GraphState &g = graph_of(h, which, layer_mask);
+    const int32_t n = h->n;
+    DevIn<uint64_t> F;
+    DevIn<uint32_t> R;
+    F.from(h, farness, n);
+    R.from(h, reach, n);
+    // validated with a flag of its own, so a refusal leaves the handle's error word and results alone
+    DBuf<int32_t> bad;
+    if (!bad.alloc(&h->al, 1)) fail(HOMLN_ENOMEM, "import flag");
+    HCUDA(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), h->stream));
+    partials_check(n, F.p, R.p, bad.p, h->stream);
+    int32_t hbad = 0;
+    HCUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    HCUDA(cudaStreamSynchronize(h->stream));
+    if (hbad) fail(HOMLN_ERANGE, "imported farness/reach cannot come from a BFS on n nodes");
+    DBuf<uint64_t> nF, sd;
+    DBuf<uint32_t> nR;
+    DBuf<double> cc;
+    DBuf<int32_t> deg;
+    if (!nF.alloc(&h->al, n) || !nR.alloc(&h->al, n) || !cc.alloc(&h->al, n) || !sd.alloc(&h->al, n) ||
+        !deg.alloc(&h->al, n))
+        fail(HOMLN_ENOMEM, "imported results");
+    HCUDA(cudaMemcpyAsync(nF.p, F.p, sizeof(uint64_t) * n, cudaMemcpyDefault, h->stream));
+    HCUDA(cudaMemcpyAsync(nR.p, R.p, sizeof(uint32_t) * n, cudaMemcpyDefault, h->stream));
+    closeness_finalize(n, in_csr(h, g).rowptr.p, nF.p, nR.p, cc.p, sd.p, deg.p, h->stream);
+    g.selections.clear();
+    g.F = std::move(nF);
+    g.R = std::move(nR);
+    g.cc = std::move(cc);
+    g.sumdist = std::move(sd);
+    g.deg = std::move(deg);
+    g.analysed = true;
     API_END
 }
 
@@ -873,18 +958,7 @@ homln_status homln_invalidate(homln_t h) {
     API_BEGIN
     if (!h) fail(HOMLN_EINVAL, "null handle");
     use_device(h);
-    auto drop = [](GraphState &g) {
-        g.analysed = false;
-        g.selections.clear();
-        g.F.release();
-        g.R.release();
-        g.cc.release();
-        g.sumdist.release();
-        g.deg.release();
-    };
-    for (auto &g : h->layers) drop(*g);
-    for (auto &kv : h->ands) drop(*kv.second);
-    for (auto &kv : h->ors) drop(*kv.second);
+    drop_results(h);
     API_END
 }
 

@@ -260,6 +260,8 @@ struct BfsTuning {
     int threads = 512;
     int blocks_per_sm = 0;
     int relabel = 1;
+    int wait_limit_ms = 2000;  // device-side waits give up after this long (HOMLN_ETIMEOUT)
+    int phantom = 0;           // tests: team barriers also wait for blocks that do not exist
 };
 
 struct BfsStats {  // filled by an instrumented run
@@ -304,6 +306,8 @@ int msbfs_pick_words(int32_t n);
 // ---------------------------------------------------------------------------
 void closeness_finalize(int32_t n, const int64_t *rowptr, const uint64_t *F, const uint32_t *R, double *cc,
                         uint64_t *sumdist, int32_t *deg, cudaStream_t s);
+// Device error DEV_RANGE unless every (F, R) pair can come from a BFS on n vertices.
+void partials_check(int32_t n, const uint64_t *F, const uint32_t *R, int32_t *d_err, cudaStream_t s);
 // Selected ids in rank order into d_out (capacity n); count to host.
 int32_t select_nodes(int32_t n, const double *d_scores, const homln_select &sel, int32_t *d_out,
                      uint32_t *d_member_bits, int32_t *d_err, Alloc *al, cudaStream_t s);

@@ -65,6 +65,8 @@ struct TeamArgs {
     int32_t *err;
     int32_t atomic_fr;          // several teams may update one graph's F/R
     unsigned long long *stats;
+    uint64_t wait_ns;           // give-up time of every barrier wait
+    int32_t phantom;            // tests: blocks every team barrier waits for in vain
 };
 
 // First vertex of a degree-descending graph whose degree is below thr (binary search).
@@ -195,9 +197,11 @@ struct TeamBarrier {
     uint32_t *gen;
     int32_t *err;
     uint32_t size;
+    uint64_t limit_ns;  // a waiter gives up after this long: DEV_TIMEOUT
 };
 
-__device__ __forceinline__ bool team_sync(const TeamBarrier &b, uint64_t limit_ns = 2000000000ull) {
+__device__ __forceinline__ bool team_sync(const TeamBarrier &b) {
+    const uint64_t limit_ns = b.limit_ns;
     if (b.size == 1) {
         __syncthreads();
         return *(volatile int32_t *)b.err == 0;
@@ -778,14 +782,15 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
         s_rank = (int)atomicAdd(A.bar + (size_t)tm * 32 + 9, 1u);
     }
     {
-        const TeamBarrier all{A.grid_bar, A.grid_bar + 1, A.err, gridDim.x};
+        const TeamBarrier all{A.grid_bar, A.grid_bar + 1, A.err, gridDim.x, A.wait_ns};
         if (!team_sync(all)) return;
     }
     const int team = s_team;
     const int rank = s_rank;
     uint32_t *tbar = A.bar + (size_t)team * 32;
     const int tsize = (int)*(volatile uint32_t *)(tbar + 9);
-    const TeamBarrier tb{tbar, tbar + 1, A.err, (uint32_t)tsize};
+    // (test_phantom_blocks: the barrier also counts blocks that never arrive, so it runs out)
+    const TeamBarrier tb{tbar, tbar + 1, A.err, (uint32_t)(tsize + A.phantom), A.wait_ns};
     const size_t stride = (size_t)A.maxn * W;
     const size_t arr = stride * A.nteams;
     uint64_t *seen = A.state + 0 * arr + team * stride;
@@ -1091,6 +1096,8 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     A.err = d_err;
     A.atomic_fr = nteams > 1 ? 1 : 0;
     A.stats = stats ? st.p : nullptr;
+    A.wait_ns = (uint64_t)t.wait_limit_ms * 1000000ull;
+    A.phantom = t.phantom;
     void *args[] = {&A};
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
     if (!plain) {

@@ -191,6 +191,17 @@ __global__ void k_finalize(int32_t n, const int64_t *__restrict__ rp, const uint
     }
 }
 
+// Imported partial results must be ones a BFS can produce: R(v) <= n-1 reached vertices, each
+// at distance 1 .. n-1 (so R <= F <= R (n-1), and F = 0 exactly when R = 0).
+__global__ void k_check_partials(int32_t n, const uint64_t *__restrict__ F, const uint32_t *__restrict__ R,
+                                 int32_t *err) {
+    const uint64_t nm1 = n > 0 ? (uint64_t)(n - 1) : 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t f = F[v], r = R[v];
+        if (r > nm1 || f < r || f > r * nm1) dev_fail(err, DEV_RANGE);
+    }
+}
+
 // ---------------------------------------------------------------- selection
 __global__ void k_score_keys(int32_t n, const double *__restrict__ sc, uint64_t *__restrict__ keys,
                              uint32_t *__restrict__ ids) {
@@ -432,6 +443,12 @@ void closeness_finalize(int32_t n, const int64_t *rowptr, const uint64_t *F, con
                         uint64_t *sumdist, int32_t *deg, cudaStream_t s) {
     if (n <= 0) return;
     launch(k_finalize, grid_for(n), 256, 0, s, n, rowptr, F, R, cc, sumdist, deg);
+    HCUDA(cudaGetLastError());
+}
+
+void partials_check(int32_t n, const uint64_t *F, const uint32_t *R, int32_t *d_err, cudaStream_t s) {
+    if (n <= 0) return;
+    launch(k_check_partials, grid_for(n), 256, 0, s, n, F, R, d_err);
     HCUDA(cudaGetLastError());
 }
 

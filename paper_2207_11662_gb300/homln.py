@@ -33,7 +33,8 @@ EXPORTS = [
     "homln_and_closeness", "homln_topk", "homln_compose", "homln_accuracy", "homln_set_profiling",
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
-    "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness",
+    "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness", "homln_export_partials",
+    "homln_import_partials",
 ]
 
 
@@ -58,7 +59,7 @@ class homln_subset_result(ctypes.Structure):
 class homln_tuning(ctypes.Structure):
     _fields_ = [("words_per_node", c_int32), ("push_alpha", c_int32), ("threads", c_int32),
                 ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("team_mix", c_int32),
-                ("schedule", c_int32)]
+                ("schedule", c_int32), ("wait_limit_ms", c_int32), ("test_phantom_blocks", c_int32)]
 
 
 class homln_profile_t(ctypes.Structure):
@@ -114,6 +115,8 @@ def _load():
         "homln_invalidate": (S, [c_void_p]),
         "homln_subset_sweep": (S, [c_void_p, c_int32, POINTER(homln_select), c_int32, POINTER(homln_subset_result),
                                    c_int32, POINTER(c_int32)]),
+        "homln_export_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p]),
+        "homln_import_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p]),
         "homln_last_error": (c_char_p, []),
         "homln_version": (c_char_p, []),
         "homln_accuracy_noalloc": (S, [c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
@@ -203,8 +206,9 @@ def homln_destroy(h) -> None:
 
 
 def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0,
-                     team_mix=0, schedule=0) -> None:
-    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix, schedule)
+                     team_mix=0, schedule=0, wait_limit_ms=0, test_phantom_blocks=0) -> None:
+    t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix, schedule,
+                     wait_limit_ms, test_phantom_blocks)
     _check(lib.homln_set_tuning(h, ctypes.byref(t)), "homln_set_tuning")
 
 
@@ -243,6 +247,16 @@ def homln_or_aggregate(h, layer_mask: int, capacity: int = 0, or_src=None, or_ds
 
 def homln_or_closeness(h, layer_mask: int, farness=None, reach=None, cc=None) -> None:
     _check(lib.homln_or_closeness(h, int(layer_mask), ptr(farness), ptr(reach), ptr(cc)), "homln_or_closeness")
+
+
+def homln_export_partials(h, which: int, layer_mask: int, farness, reach, degree=None) -> None:
+    _check(lib.homln_export_partials(h, int(which), int(layer_mask), ptr(farness), ptr(reach), ptr(degree)),
+           "homln_export_partials")
+
+
+def homln_import_partials(h, which: int, layer_mask: int, farness, reach) -> None:
+    _check(lib.homln_import_partials(h, int(which), int(layer_mask), ptr(farness), ptr(reach)),
+           "homln_import_partials")
 
 
 def homln_topk(h, which: int, layer_mask: int, sel, nodes_out) -> int:
@@ -387,6 +401,30 @@ class Network:
 
     def accuracy(self, pred, truth) -> dict:
         return homln_accuracy(self.h, pred, int(pred.shape[0]), truth, int(truth.shape[0]))
+
+    def save_partials(self, path: str, masks=()) -> None:
+        """Checkpoint the Psi results of every layer and of the AND graphs of `masks` (host .npz)."""
+        out = {"n": np.array([self.n]), "layers": np.array([self.n_layers])}
+        items = [(i, 0) for i in range(self.n_layers)] + [(-1, int(m)) for m in masks]
+        for which, mask in items:
+            F, R, d = np.empty(self.n, np.uint64), np.empty(self.n, np.uint32), np.empty(self.n, np.int32)
+            homln_export_partials(self.h, which, mask, F, R, d)
+            key = f"layer{which}" if which >= 0 else f"and{mask}"
+            out[key + "_F"], out[key + "_R"], out[key + "_deg"] = F, R, d
+        np.savez(path, **out)
+
+    def load_partials(self, path: str) -> None:
+        """Resume from save_partials: later queries on those graphs run no BFS."""
+        z = np.load(path)
+        if int(z["n"][0]) != self.n or int(z["layers"][0]) != self.n_layers:
+            raise ValueError("checkpoint was taken on a different network")
+        for key in z.files:
+            if not key.endswith("_F"):
+                continue
+            base = key[:-2]
+            which, mask = (int(base[5:]), 0) if base.startswith("layer") else (-1, int(base[3:]))
+            homln_import_partials(self.h, which, mask, np.ascontiguousarray(z[base + "_F"]),
+                                  np.ascontiguousarray(z[base + "_R"]))
 
     def close(self):
         if getattr(self, "h", None):

@@ -537,3 +537,56 @@ def test_large_ba_full_size_sampled(H):
     for i in range(L):
         assert set(naive.tolist()) <= set(g.topk(i, 1, sel).cpu().numpy().tolist())
     g.close()
+
+
+def test_bounded_wait_runs_out_and_the_handle_recovers(H):
+    """Failure detection: team barriers that wait for blocks that do not exist give up after the
+    wait limit; the call reports HOMLN_ETIMEOUT, the handle drops its results and stays usable."""
+    import time
+    net = synth.homln_small_overlap(700, 6.0, 2, 0.4, 44)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    g = H.Network(net.n, to_dev(net.layers))
+    H.homln_set_tuning(g.h, wait_limit_ms=100, test_phantom_blocks=1)
+    t0 = time.perf_counter()
+    with pytest.raises(H.HomlnError) as e:
+        g.layer_closeness(0)
+        H.homln_sync(g.h)
+    assert e.value.code == H.HOMLN_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    H.homln_set_tuning(g.h)
+    for i in range(2):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    check_graph(*g.and_closeness(3), ref.and_graph(3))
+    g.close()
+
+
+def test_checkpoint_and_resume_of_partials(H, tmp_path):
+    """Export the Psi results of every layer and the AND graph, import them into a fresh handle:
+    compositions and the ground truth match without running a BFS; impossible values are refused."""
+    net = synth.homln_small_overlap(900, 7.0, 3, 0.5, 66)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    sel, osel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)
+    a = H.Network(net.n, to_dev(net.layers))
+    path = str(tmp_path / "partials.npz")
+    a.save_partials(path, masks=(7, 3))
+    a.close()
+    b = H.Network(net.n, to_dev(net.layers))
+    H.homln_set_profiling(b.h, True, False)
+    b.load_partials(path)
+    for i in range(3):
+        check_graph(*b.layer_closeness(i), ref.layer(i))
+    check_graph(*b.and_closeness(7), ref.and_graph(7))
+    assert b.topk(-1, 7, sel).cpu().numpy().tolist() == ref.topk(-1, 7, osel).tolist()
+    for heur in (0, 1, 2):
+        assert b.compose(7, heur, sel).cpu().numpy().tolist() == ref.compose(7, heur, osel).tolist()
+    assert H.homln_get_profile(b.h)["bfs_launches"] == 0
+    # a reach larger than n - 1 cannot come from a BFS: refused, the imported results stay
+    z = np.load(path)
+    bad = np.ascontiguousarray(z["layer0_R"]).copy()
+    bad[5] = net.n
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_import_partials(b.h, 0, 0, np.ascontiguousarray(z["layer0_F"]), bad)
+    assert e.value.code == H.HOMLN_ERANGE
+    check_graph(*b.layer_closeness(0), ref.layer(0))
+    assert H.homln_get_profile(b.h)["bfs_launches"] == 0
+    b.close()
