@@ -209,20 +209,21 @@ void lanes_open(homln_t h) {
     HCUDA(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
 }
 
-// The first `count` lanes wait for everything queued so far on the handle's stream.
+// When `count` > 0 work items follow: every lane waits for everything queued so far on the
+// handle's stream (all lanes, not only the ones the items use: a buffer a lane owns may be
+// freed on it by an item, after the handle's stream last used it).
 void lanes_fork(homln_t h, int count) {
     Lanes &L = h->lanes;
-    count = std::min(count, Lanes::kCount);
     if (count <= 0) return;
     HCUDA(cudaEventRecord(L.fork, h->stream));
-    for (int i = 0; i < count; ++i) HCUDA(cudaStreamWaitEvent(L.s[i], L.fork, 0));
+    for (int i = 0; i < Lanes::kCount; ++i) HCUDA(cudaStreamWaitEvent(L.s[i], L.fork, 0));
 }
 
-// The handle's stream waits for everything queued so far on the first `count` lanes.
+// After `count` > 0 work items: the handle's stream waits for everything queued on the lanes.
 void lanes_join(homln_t h, int count) {
     Lanes &L = h->lanes;
-    count = std::min(count, Lanes::kCount);
-    for (int i = 0; i < count; ++i) {
+    if (count <= 0) return;
+    for (int i = 0; i < Lanes::kCount; ++i) {
         HCUDA(cudaEventRecord(L.done[i], L.s[i]));
         HCUDA(cudaStreamWaitEvent(h->stream, L.done[i], 0));
     }
@@ -340,6 +341,18 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
         jobs.push_back(BfsJob{&g->bfs, g->F.p, g->R.p});
         if (o != h && o->stream != h->stream && std::find(others.begin(), others.end(), o) == others.end())
             others.push_back(o);
+    }
+    // Rebuilding a BFS graph (its relabelling setting changed) frees the old one on the stream
+    // that owns it, which need not be ordered after the launches that read it: wait for the
+    // device first (a rare path).
+    bool rebuild = false;
+    for (const auto &it : prep) rebuild |= it.second->bfs_ready;
+    if (rebuild) {
+        HCUDA(cudaDeviceSynchronize());
+        for (const auto &it : prep) {
+            it.second->bfs = BfsGraph();
+            it.second->bfs_ready = false;
+        }
     }
     // the relabellings of h's graphs run on h's lanes side by side; other handles' on their streams
     int nl = 0;

@@ -590,3 +590,18 @@ def test_checkpoint_and_resume_of_partials(H, tmp_path):
     check_graph(*b.layer_closeness(0), ref.layer(0))
     assert H.homln_get_profile(b.h)["bfs_launches"] == 0
     b.close()
+
+
+def test_relabel_setting_changed_between_analyses(H):
+    """The BFS graphs are rebuilt when the relabelling setting changes on a live handle."""
+    net = synth.homln_small_overlap(1100, 6.0, 3, 0.4, 87)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    g = H.Network(net.n, to_dev(net.layers))
+    for relabel in (1, 0, 1):
+        H.homln_set_tuning(g.h, relabel=relabel)
+        H.homln_invalidate(g.h)
+        H.homln_analyse(g.h, 7, True)
+        for i in range(3):
+            check_graph(*g.layer_closeness(i), ref.layer(i))
+        check_graph(*g.and_closeness(7), ref.and_graph(7))
+    g.close()
