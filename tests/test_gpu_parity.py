@@ -605,3 +605,20 @@ def test_relabel_setting_changed_between_analyses(H):
             check_graph(*g.layer_closeness(i), ref.layer(i))
         check_graph(*g.and_closeness(7), ref.and_graph(7))
     g.close()
+
+
+def test_batch_of_many_small_handles(H):
+    """40 handles (each with its own side streams) analysed in one launch, then per handle."""
+    nets = synth.homln_batch(count=40, seed=97, n_range=(150, 700), layer_range=(2, 5))
+    gs = [H.Network(net.n, to_dev(net.layers)) for net in nets]
+    masks = [(1 << net.n_layers) - 1 for net in nets]
+    sel, osel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)
+    H.homln_batch_analyse([g.h for g in gs], masks, True)
+    for g, net, mask in zip(gs, nets, masks):
+        ref = O.OracleHoMLN(net.n, net.layers)
+        for i in range(net.n_layers):
+            check_graph(*g.layer_closeness(i), ref.layer(i))
+        check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+        assert g.compose(mask, 2, sel).cpu().numpy().tolist() == ref.compose(mask, 2, osel).tolist()
+    for g in gs:
+        g.close()
