@@ -520,12 +520,12 @@ def serving(args, dev):
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         items = pool.map(_serving_item, [(i, r["spec"], r["t"]) for i, r in enumerate(specs)], chunksize=4)
     reqs = [serve.Request(i, n, layers, arrival=t, teps_work=w) for i, n, layers, t, w in items]
-    srv = serve.Server(device=dev.index or 0, workers=2, max_wave=16, mem_budget_bytes=32 << 30)
+    srv = serve.Server(device=dev.index or 0, workers=1, max_wave=16, mem_budget_bytes=32 << 30)
     t0 = time.perf_counter()
     done = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
     out = serve.latency_stats(done, wall)
-    out.update({"duration_s": round(wall, 2), "rate_req_per_s": args.serve_rate, "workers": 2, "max_wave": 16,
+    out.update({"duration_s": round(wall, 2), "rate_req_per_s": args.serve_rate, "workers": 1, "max_wave": 16,
                 "waves": srv.waves, "errors": srv.errors[:3],
                 "workload": "Poisson arrivals, HoMLNs of 2-6 layers, n log-uniform in [1e3, 1e5], ER or "
                             "Chung-Lu layers (avg deg 6-12); per request: Psi of all layers + AND, top-10% ground "

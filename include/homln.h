@@ -139,6 +139,10 @@ typedef struct homln_tuning {
     int32_t test_phantom_blocks; /* failure-detection tests only: every team barrier of the
                                 persistent BFS also waits for this many blocks that do not exist,
                                 so its wait runs out after wait_limit_ms (0 = off) */
+    int32_t max_tiles_per_launch; /* the persistent BFS takes at most this many (graph, batch) tiles
+                                per launch and launches again for the rest, so that work on other
+                                streams (e.g. a higher-priority one) can run in between; identical
+                                results (0 = all tiles in one launch) */
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.

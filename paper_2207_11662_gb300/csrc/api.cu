@@ -200,8 +200,13 @@ void use_device(homln_t h) { HCUDA(cudaSetDevice(h->device)); }
 
 void lanes_open(homln_t h) {
     Lanes &L = h->lanes;
+    int prio = 0;  // the lanes run at the priority of the handle's stream
+    if (cudaStreamGetPriority(h->stream, &prio) != cudaSuccess) {
+        cudaGetLastError();
+        prio = 0;
+    }
     for (int i = 0; i < Lanes::kCount; ++i) {
-        HCUDA(cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking));
+        HCUDA(cudaStreamCreateWithPriority(&L.s[i], cudaStreamNonBlocking, prio));
         HCUDA(cudaEventCreateWithFlags(&L.done[i], cudaEventDisableTiming));
         L.al[i].a = h->al.a;
         L.al[i].stream = L.s[i];
@@ -652,6 +657,8 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         if (t->test_phantom_blocks < 0 || t->test_phantom_blocks > 1024)
             fail(HOMLN_EINVAL, "test_phantom_blocks must be in [0, 1024]");
         bt.phantom = t->test_phantom_blocks;
+        if (t->max_tiles_per_launch < 0) fail(HOMLN_EINVAL, "max_tiles_per_launch must be >= 0");
+        bt.max_tiles = t->max_tiles_per_launch;
     }
     h->tuning = bt;
     API_END

@@ -262,6 +262,7 @@ struct BfsTuning {
     int relabel = 1;
     int wait_limit_ms = 2000;  // device-side waits give up after this long (HOMLN_ETIMEOUT)
     int phantom = 0;           // tests: team barriers also wait for blocks that do not exist
+    int max_tiles = 0;         // persistent launches take at most this many tiles each (0 = all)
 };
 
 struct BfsStats {  // filled by an instrumented run

@@ -938,6 +938,8 @@ PhaseKernel phase_kernel_for(int W, bool stats) {
     }
 }
 
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+
 __global__ void k_scatter_back(int32_t n, const int32_t *__restrict__ perm, const uint64_t *__restrict__ Fi,
                                const uint32_t *__restrict__ Ri, uint64_t *__restrict__ F, uint32_t *__restrict__ R) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1101,8 +1103,19 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     void *args[] = {&A};
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
     if (!plain) {
-        g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-        HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
+        // max_tiles: the tiles go out in several launches of at most that many, so that work of
+        // other streams (a higher-priority one, say) can run in between
+        const int32_t chunk = t.max_tiles > 0 ? t.max_tiles : tile;
+        for (int32_t c0 = 0; c0 < tile; c0 += chunk) {
+            if (c0 > 0) {  // fresh barriers, counters and team formation; the queue resumes at c0
+                HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
+                HCUDA(cudaMemsetAsync(barmem.p, 0, bar_words * sizeof(uint32_t), s));
+                launch(k_set_i32, 1, 1, 0, s, queue.p, c0);
+            }
+            A.ntiles = (int32_t)std::min<int64_t>(tile, (int64_t)c0 + chunk);
+            g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+            HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
+        }
     } else {
         // plain schedule: one launch per phase, the host reads the level counters after every level
         uint32_t ps = 0;

@@ -10,14 +10,22 @@ Scheduling:
     estimated device footprints of the requests in flight stays under the budget;
     a request that can never fit is rejected (HOMLN_ENOMEM) at once;
   * continuous batching: worker threads, each with its own CUDA stream, repeatedly
-    take every admitted request that is waiting (up to ``max_wave``) and run them as
-    one wave: CSR builds, then one persistent BFS launch over all (graph, source
-    batch) tiles of the wave (homln_batch_analyse) on the whole GPU, then selection,
+    take admitted requests that are waiting (up to ``max_wave``) and run them as one
+    wave: CSR builds, then persistent BFS launches over all (graph, source batch)
+    tiles of the wave (homln_batch_analyse) on the whole GPU, then selection,
     composition and accuracy. Requests that arrive while a wave is on the GPU join
-    the next wave of any free worker; a second worker prepares its wave (CSR builds,
-    selections) while the other's BFS runs. Measured on GB300 at 50 requests/s:
-    whole-GPU waves with two workers gave p50 9 ms / p99 127 ms, against 26 ms /
-    326 ms for three workers whose waves took one block per SM each.
+    the next wave of a free worker;
+  * size classes: a request is "big" when its BFS work (nodes x edges) exceeds
+    ``big_work``. One worker (the default) takes waves in arrival order across the
+    classes. With two or more workers, one serves only small requests on a
+    high-priority stream; the others take big requests first (then small ones) on
+    low-priority streams and split a big wave's BFS into launches of at most
+    ``big_max_tiles`` tiles, so that the GPU can take up small waves between them.
+    Measured on GB300 at 50 requests/s (config 5): one worker p50 8.4-9.0 ms / p99
+    119-122 ms; two workers in arrival order 9.0 / 127 ms; the class split with two
+    workers 10.4-14.9 / 136-183 ms (smaller launches were worse); three workers whose
+    waves took one block per SM each 26 / 326 ms. The largest requests' own service
+    time (up to ~4e11 edge visits) sets the p99.
 
 Every GPU step runs in libhomln.so; this module only schedules.
 """
@@ -68,42 +76,61 @@ def footprint_bytes(n: int, edge_counts) -> int:
     return int(csr + build + outputs + bfs_state + (1 << 20))
 
 
+SMALL, BIG = 0, 1
+
+
 class Admission:
-    """FIFO admission under a device-memory budget (host logic only)."""
+    """FIFO admission per size class under one device-memory budget (host logic only)."""
 
     def __init__(self, budget_bytes: int):
         self.budget = int(budget_bytes)
         self.in_use = 0
-        self.waiting = collections.deque()
+        self.queues = (collections.deque(), collections.deque())  # SMALL, BIG
         self.lock = threading.Lock()
         self.cv = threading.Condition(self.lock)
         self.closed = False
 
-    def submit(self, req: Request, need: int) -> bool:
+    @property
+    def waiting(self):
+        return list(self.queues[SMALL]) + list(self.queues[BIG])
+
+    def submit(self, req: Request, need: int, cls: int = SMALL) -> bool:
         """Queue a request; False (and no queueing) if it can never fit."""
         with self.cv:
             if need > self.budget:
                 return False
-            self.waiting.append((req, need))
+            self.queues[cls].append((req, need))
             self.cv.notify_all()
             return True
 
-    def take(self, max_items: int, timeout: float):
-        """Admit the longest FIFO prefix that fits (at least one item when it fits); blocks up to timeout."""
+    def _prefix(self, q, max_items):
+        out = []
+        while q and len(out) < max_items:
+            req, need = q[0]
+            if self.in_use + need > self.budget:
+                break
+            q.popleft()
+            self.in_use += need
+            out.append((req, need))
+        return out
+
+    def take(self, max_items: int, timeout: float, classes=None):
+        """Admit the longest FIFO prefix that fits (at least one item when it fits) of the first
+        class in `classes` that has one -- or, with classes=None, of the class whose oldest request
+        was submitted first (FIFO across classes); blocks up to timeout. None once closed and
+        drained."""
         deadline = time.monotonic() + timeout
         with self.cv:
             while True:
-                out = []
-                while self.waiting and len(out) < max_items:
-                    req, need = self.waiting[0]
-                    if self.in_use + need > self.budget:
-                        break
-                    self.waiting.popleft()
-                    self.in_use += need
-                    out.append((req, need))
-                if out:
-                    return out
-                if self.closed and not self.waiting:
+                order = classes
+                if order is None:
+                    heads = [(q[0][0].t_submit, c) for c, q in enumerate(self.queues) if q]
+                    order = [c for _, c in sorted(heads)]
+                for cls in order:
+                    out = self._prefix(self.queues[cls], max_items)
+                    if out:
+                        return out
+                if self.closed and not any(self.queues[c] for c in (classes or (SMALL, BIG))):
                     return None
                 left = deadline - time.monotonic()
                 if left <= 0:
@@ -121,14 +148,22 @@ class Admission:
             self.cv.notify_all()
 
 
+def work_estimate(n: int, edge_counts) -> int:
+    """BFS work of a request, nodes x edges over its layers (a bound on its edge visits / 2)."""
+    return int(n) * int(sum(edge_counts))
+
+
 class Server:
-    def __init__(self, device: int = 0, workers: int = 2, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
-                 percent: float = 10.0, keep_farness: bool = False, tuning: dict | None = None):
+    def __init__(self, device: int = 0, workers: int = 1, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
+                 percent: float = 10.0, keep_farness: bool = False, tuning: dict | None = None,
+                 big_work: float = 2e10, big_max_tiles: int = 64):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.workers = workers
         self.max_wave = max_wave
+        self.big_work = big_work
+        self.big_max_tiles = big_max_tiles
         self.adm = Admission(mem_budget_bytes)
         self.sel = H.make_select(H.HOMLN_TOPK_PERCENT, percent)
         self.keep_farness = keep_farness
@@ -140,7 +175,7 @@ class Server:
         self.errors = []
 
     # ---------------------------------------------------------------- workers
-    def _run_wave(self, items, stream, wave_id):
+    def _run_wave(self, items, stream, wave_id, tuning):
         reqs = [r for r, _ in items]
         t_admit = time.perf_counter() - self.t0
         handles = []
@@ -149,7 +184,7 @@ class Server:
                 r.t_admit = t_admit
                 r.wave = wave_id
                 handles.append(H.homln_create(r.n, r.layers, stream=stream.cuda_stream))
-            H.homln_set_tuning(handles[0], **self.tuning)
+            H.homln_set_tuning(handles[0], **tuning)
             masks = [(1 << len(r.layers)) - 1 for r in reqs]
             H.homln_batch_analyse(handles, masks, True)
             for r, h, mask in zip(reqs, handles, masks):
@@ -185,9 +220,16 @@ class Server:
     def _worker(self, idx):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(self.device)
+        # worker 0 of two or more serves small requests only, at high priority; the others take
+        # big requests first, at low priority, with their BFS split into launches
+        small_only = self.workers >= 2 and idx == 0
+        classes = (SMALL,) if small_only else (BIG, SMALL) if self.workers >= 2 else None
+        stream = torch.cuda.Stream(self.device, priority=-1 if small_only else 0)
+        tuning = dict(self.tuning)
+        if not small_only and self.workers >= 2:
+            tuning.setdefault("max_tiles_per_launch", self.big_max_tiles)
         while True:
-            items = self.adm.take(self.max_wave, timeout=0.05)
+            items = self.adm.take(self.max_wave, timeout=0.05, classes=classes)
             if items is None:
                 return
             if not items:
@@ -196,14 +238,16 @@ class Server:
                 wave_id = self.waves
                 self.waves += 1
             try:
-                self._run_wave(items, stream, wave_id)
+                self._run_wave(items, stream, wave_id, tuning)
             except Exception as e:  # keep serving; record the failure
                 self.errors.append(repr(e))
 
     # ---------------------------------------------------------------- driver
     def submit(self, req: Request):
         req.t_submit = time.perf_counter() - self.t0
-        if not self.adm.submit(req, footprint_bytes(req.n, [s.shape[0] for s, _ in req.layers])):
+        counts = [s.shape[0] for s, _ in req.layers]
+        cls = BIG if work_estimate(req.n, counts) > self.big_work else SMALL
+        if not self.adm.submit(req, footprint_bytes(req.n, counts), cls):
             req.status, req.error = H.HOMLN_ENOMEM, ENOMEM_REJECT
             req.t_admit = req.t_done = req.t_submit
             with self.done_lock:

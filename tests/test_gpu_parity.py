@@ -622,3 +622,11 @@ def test_batch_of_many_small_handles(H):
         assert g.compose(mask, 2, sel).cpu().numpy().tolist() == ref.compose(mask, 2, osel).tolist()
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("max_tiles", [1, 3, 7])
+def test_tiles_split_over_several_launches(H, max_tiles):
+    """max_tiles_per_launch: the persistent BFS runs in several launches; results are identical."""
+    net = synth.homln_small_overlap(2100, 6.0, 3, 0.4, 93)
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    full_parity(H, net, sel, tuning=dict(max_tiles_per_launch=max_tiles, words_per_node=2), heuristics=(2,))

@@ -52,3 +52,33 @@ def test_waiters_wake_on_release():
 def test_footprint_grows_with_size():
     serve = _mods()
     assert serve.footprint_bytes(1000, [4000, 4000]) < serve.footprint_bytes(100000, [400000, 400000, 400000])
+
+
+def test_size_classes_keep_fifo_order_within_a_class():
+    serve = _mods()
+    a = serve.Admission(1000)
+    small = [serve.Request(i, 10, []) for i in range(3)]
+    big = [serve.Request(10 + i, 10, []) for i in range(2)]
+    for r in (small[0], big[0], small[1], big[1], small[2]):
+        a.submit(r, 10, serve.BIG if r.rid >= 10 else serve.SMALL)
+    assert [r.rid for r, _ in a.take(8, 0.01, classes=(serve.SMALL,))] == [0, 1, 2]
+    assert a.take(8, 0.01, classes=(serve.SMALL,)) == []
+    assert [r.rid for r, _ in a.take(8, 0.01, classes=(serve.BIG, serve.SMALL))] == [10, 11]
+    a.close()
+    assert a.take(8, 0.01, classes=(serve.SMALL,)) is None
+
+
+def test_work_estimate_splits_the_classes():
+    serve = _mods()
+    assert serve.work_estimate(1000, [4000, 4000]) < 2e10 < serve.work_estimate(100000, [500000] * 4)
+
+
+def test_single_worker_takes_the_oldest_class_first():
+    serve = _mods()
+    a = serve.Admission(1000)
+    reqs = [serve.Request(i, 10, []) for i in range(3)]
+    for r, t, cls in zip(reqs, (0.3, 0.1, 0.2), (serve.SMALL, serve.BIG, serve.SMALL)):
+        r.t_submit = t
+        a.submit(r, 10, cls)
+    assert [r.rid for r, _ in a.take(8, 0.01)] == [1]  # the big request arrived first
+    assert [r.rid for r, _ in a.take(8, 0.01)] == [0, 2]
