@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-paper-like", action="store_true", help="skip the paper-shaped accuracy/timing runs")
+    p.add_argument("--no-widened", action="store_true",
+                   help="skip the OR-aggregation, subset-sweep and directed-layer measurements")
     p.add_argument("--serve-seconds", type=float, default=15.0)
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--single-bfs", action="store_true",
@@ -500,6 +502,92 @@ def paper_like(args, dev):
     return out
 
 
+def _components_teps(n: int, lo, hi) -> int:
+    """sum over the components of an undirected graph of n_c * m_c (edges as pairs lo < hi)."""
+    import scipy.sparse as sps
+    from scipy.sparse.csgraph import connected_components
+    A = sps.coo_matrix((np.ones(lo.shape[0]), (lo, hi)), shape=(n, n)).tocsr()
+    nc, lab = connected_components(A, directed=False)
+    nodes = np.bincount(lab, minlength=nc).astype(np.int64)
+    edges = np.bincount(lab[lo], minlength=nc).astype(np.int64)
+    return int(np.sum(nodes * edges))
+
+
+def widened(args, dev, reps: int = 3):
+    """The follow-on rows on the power-law n=50,000 workload: the OR-aggregated ground truth, the
+    layer-subset sweep, and the same network with directed layers."""
+    import torch
+    from paper_2207_11662_gb300 import homln as H
+    from paper_2207_11662_gb300 import synth
+    net, _ = make_workload("powerlaw50k", 0)
+    n, L = net.n, net.n_layers
+    full = (1 << L) - 1
+    stream = torch.cuda.current_stream(dev)
+    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0)
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    dl = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
+    F = torch.empty(n, dtype=torch.int64, device=dev)
+    out = {}
+    # OR aggregation: build the OR graph and run its all-sources BFS (a fresh handle each time)
+    def or_step():
+        h = H.homln_create(n, dl, stream=stream.cuda_stream)
+        H.homln_or_closeness(h, full, F, None, None)
+        H.homln_destroy(h)
+    h = H.homln_create(n, dl, stream=stream.cuda_stream)
+    m_or = H.homln_or_aggregate(h, full)
+    s_or = np.empty(m_or, np.int32)
+    d_or = np.empty(m_or, np.int32)
+    H.homln_or_aggregate(h, full, m_or, s_or, d_or)
+    H.homln_destroy(h)
+    ms = timed(or_step)
+    work = _components_teps(n, s_or.astype(np.int64), d_or.astype(np.int64))
+    out["or_aggregation"] = {"ms": round(ms, 3), "edges": int(m_or), "gteps": round(work / ms / 1e6, 1),
+                             "includes": "CSR builds of 4 layers, OR union, relabelling, all-sources BFS"}
+    # layer-subset sweep: ground truth, CC2 estimate and accuracy of all 11 subsets of >= 2 layers
+    def sweep():
+        h = H.homln_create(n, dl, stream=stream.cuda_stream)
+        res = H.homln_subset_sweep(h, H.HOMLN_CC2, sel, 2)
+        H.homln_destroy(h)
+        return res
+    res = sweep()
+    ms = timed(sweep)
+    out["subset_sweep"] = {"ms": round(ms, 3), "subsets": len(res),
+                           "mean_jaccard_cc2": round(float(np.mean([r["jaccard"] for r in res])), 4),
+                           "includes": "CSR builds, BFS of 4 layers + 11 AND graphs in one launch, "
+                                       "11 x (ground truth, CC2, accuracy)"}
+    # directed layers: each edge a random-direction arc, plus the reverse of 25% of them
+    arcs = [synth.with_reciprocal(e, 0.25, 7001 + i) for i, e in enumerate(net.layers)]
+    da = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in arcs]
+    def directed_step():
+        h = H.homln_create(n, da, stream=stream.cuda_stream, directed=True)
+        H.homln_analyse(h, full, True)
+        H.homln_destroy(h)
+    ms = timed(directed_step)
+    h = H.homln_create(n, da, stream=stream.cuda_stream, directed=True)
+    m_and = H.homln_and_aggregate(h, full)
+    H.homln_destroy(h)
+    n_arcs = [int(np.unique(s.astype(np.int64)[s != d] * n + d[s != d]).shape[0]) for s, d in arcs]
+    bound = n * (sum(n_arcs) + m_and)
+    out["directed"] = {"ms": round(ms, 3), "arcs_per_layer": n_arcs, "and_arcs": int(m_and),
+                       "gteps_bound": round(bound / ms / 1e6, 1),
+                       "includes": "CSR builds (out- and in-edges) of 4 layers, AND, relabelling, in-closeness "
+                                   "BFS of 4 layers + AND",
+                       "teps_convention": "n x arcs per graph: an upper bound on the arcs the BFS traverses"}
+    return out
+
+
 def _serving_item(arg):
     """Spawn-pool worker: one request's HoMLN (raw edge lists) and its TEPS work."""
     i, spec, arrival = arg
@@ -602,6 +690,8 @@ def main():
             result["serving"] = serving(args, dev)
         if not args.no_paper_like and world == 1:
             result["paper_like"] = paper_like(args, dev)
+        if not args.no_widened and world == 1:
+            result["widened"] = widened(args, dev)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources)
         print(json.dumps(result))
