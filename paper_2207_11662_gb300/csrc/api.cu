@@ -8,6 +8,8 @@
 // aggregate of the selected layers, analysed the same way.
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -168,7 +170,16 @@ struct homln_s {
 
 namespace {
 
-#define API_BEGIN try {
+// Every entry point is an NVTX range named after it (visible in nsys/ncu timelines; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+#define API_BEGIN                        \
+    const NvtxRange nvtx_range_(__func__); \
+    try {
 #define API_END                                           \
     }                                                     \
     catch (const homln::Error &e) {                       \
