@@ -430,6 +430,11 @@ def batch_vs_plain(args, dev):
     timed(lambda: H.homln_batch_analyse(hs, masks, True), reps=1)  # warm-up
     t_batch = timed(lambda: H.homln_batch_analyse(hs, masks, True))
     ref = collect()
+    # the same analysis captured once in a CUDA graph and replayed
+    graph = H.homln_graph_capture(hs, masks, True)
+    t_graph = timed(lambda: H.homln_graph_launch(graph))
+    same_graph = all(torch.equal(a, b) for x, y in zip(ref, collect()) for a, b in zip(x, y))
+    H.homln_graph_destroy(graph)
     for h in hs:
         H.homln_set_tuning(h)
     t_per = timed(lambda: [H.homln_analyse(h, m, True) for h, m in zip(hs, masks)])
@@ -437,13 +442,15 @@ def batch_vs_plain(args, dev):
     for h in hs:
         H.homln_set_tuning(h, schedule=1)
     t_plain = timed(lambda: [H.homln_analyse(h, m, True) for h, m in zip(hs, masks)], reps=1)
-    same = same and all(torch.equal(a, b) for x, y in zip(ref, collect()) for a, b in zip(x, y))
+    same = same and same_graph and all(torch.equal(a, b) for x, y in zip(ref, collect()) for a, b in zip(x, y))
     for h in hs:
         H.homln_destroy(h)
     return {"workload": f"{len(nets)} HoMLNs, {sum(n.n_layers for n in nets)} layers + {len(nets)} AND graphs, "
                         f"n in [{min(ns)}, {max(ns)}], ER/BA layers",
-            "batched_ms": round(t_batch, 3), "per_homln_persistent_ms": round(t_per, 3),
+            "batched_ms": round(t_batch, 3), "graph_replay_ms": round(t_graph, 3),
+            "per_homln_persistent_ms": round(t_per, 3),
             "plain_ms": round(t_plain, 3), "speedup_vs_plain": round(t_plain / t_batch, 2),
+            "graph_speedup_vs_plain": round(t_plain / t_graph, 2),
             "speedup_vs_per_homln": round(t_per / t_batch, 2), "batched_gteps": round(work / t_batch / 1e6, 1),
             "identical_outputs": bool(same), "autotuned": tuning,
             "autotune_candidates_ms": tune_log["candidates"]}

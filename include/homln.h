@@ -49,6 +49,9 @@ extern "C" {
 #define HOMLN_API
 #endif
 
+/* Opaque handle of a captured analysis (homln_graph_capture). */
+typedef struct homln_graph_s *homln_graph_t;
+
 /* Opaque handle: one HoMLN resident on one GPU. */
 typedef struct homln_s *homln_t;
 
@@ -193,6 +196,27 @@ HOMLN_API homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t wit
  * Results are cached in each handle exactly as homln_analyse would cache them.
  * Errors: EINVAL (null handle, masks, devices), ENOMEM, ECUDA. */
 HOMLN_API homln_status homln_batch_analyse(homln_t *nets, int32_t count, const uint64_t *masks, int32_t with_and);
+
+/* Capture the analysis that homln_batch_analyse would run (every layer in masks[i] and, with
+ * with_and != 0, the AND graph of masks[i], for every handle nets[i]) into a CUDA graph. All
+ * preparation happens here, once: CSR and AND builds, relabelling, result buffers and the BFS
+ * state. The graph holds the zeroing, the persistent BFS launch(es), the scatter-back and the
+ * closeness finalize, so a replay allocates nothing and copies nothing from the host. It runs
+ * on nets[0]'s stream with nets[0]'s tuning and error word. While the graph exists, the
+ * results of its graphs stay allocated (homln_invalidate only marks them stale), homln_destroy
+ * of its handles fails with HOMLN_EBUSY, and changing the relabelling setting fails with
+ * HOMLN_EBUSY. Errors: EINVAL (null pointers, masks, devices, the plain schedule or an
+ * instrumented handle, neither of which can be captured), ENOMEM, ECUDA (capture refused). */
+HOMLN_API homln_status homln_graph_capture(homln_t *nets, int32_t count, const uint64_t *masks, int32_t with_and,
+                                           homln_graph_t *out);
+
+/* Replay a captured analysis (asynchronous on nets[0]'s stream; the other handles' streams
+ * are ordered around it with events). Afterwards the results are cached exactly as after
+ * homln_batch_analyse. Device errors surface at the next synchronising call. */
+HOMLN_API homln_status homln_graph_launch(homln_graph_t g);
+
+/* Wait for the graph's replays and release it. NULL is a no-op. */
+HOMLN_API homln_status homln_graph_destroy(homln_graph_t g);
 
 /* Boolean AND aggregation of the layers in `layer_mask` (Section 3.1, Section 4 ground truth):
  * an edge is kept iff it is present in every selected layer. The AND graph is built

@@ -115,6 +115,7 @@ struct GraphState {
     std::map<SelKey, std::unique_ptr<Selection>> selections;
     BfsGraph bfs;          // the graph as the BFS reads it (built once, kept by homln_invalidate)
     bool bfs_ready = false;
+    int graph_refs = 0;    // captured graphs that write this graph's results (buffers stay put)
 };
 
 }  // namespace homln
@@ -143,6 +144,8 @@ struct Lanes {
     }
 };
 
+struct homln_graph_s;
+
 struct homln_s {
     Lanes lanes;
     Alloc al;  // declared before the buffers: destroyed after every buffer that uses it
@@ -159,6 +162,7 @@ struct homln_s {
     bool instrument = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     long long bfs_launches = 0;
+    int live_graphs = 0;  // captured graphs that involve this handle
     BfsStats stats;
     ~homln_s() {
         for (auto &e : events) {
@@ -258,6 +262,7 @@ void drop_results(homln_t h) {
     auto drop = [](GraphState &g) {
         g.analysed = false;
         g.selections.clear();
+        if (g.graph_refs > 0) return;  // a captured graph writes into these buffers
         g.F.release();
         g.R.release();
         g.cc.release();
@@ -333,16 +338,11 @@ struct DevOut {
     }
 };
 
-// Psi for every (handle, graph) item not analysed yet, in one persistent BFS launch on the
-// stream of `h` (the other handles' streams are ordered around it with events). Each graph's
-// outputs are allocated through its own handle.
-void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>> &items) {
-    std::vector<std::pair<homln_t, GraphState *>> todo;
-    for (const auto &it : items)
-        if (!it.second->analysed &&
-            std::find_if(todo.begin(), todo.end(), [&](const auto &x) { return x.second == it.second; }) == todo.end())
-            todo.push_back(it);
-    if (todo.empty()) return;
+using Items = std::vector<std::pair<homln_t, GraphState *>>;
+
+// Make every graph of `todo` ready for a BFS launch on h's stream: result buffers allocated
+// (kept if they exist), BFS graphs built, other handles' streams ordered before h's.
+std::vector<BfsJob> prepare_items(homln_t h, const Items &todo) {
     std::vector<BfsJob> jobs;
     std::vector<homln_t> others;
     std::vector<std::pair<homln_t, GraphState *>> prep;  // graphs whose BFS form must be (re)built
@@ -350,8 +350,9 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
         homln_t o = it.first;
         GraphState *g = it.second;
         const int32_t n = o->n;
-        if (!g->F.alloc(&o->al, n) || !g->R.alloc(&o->al, n) || !g->cc.alloc(&o->al, n) ||
-            !g->sumdist.alloc(&o->al, n) || !g->deg.alloc(&o->al, n))
+        if ((!g->F.p && !g->F.alloc(&o->al, n)) || (!g->R.p && !g->R.alloc(&o->al, n)) ||
+            (!g->cc.p && !g->cc.alloc(&o->al, n)) || (!g->sumdist.p && !g->sumdist.alloc(&o->al, n)) ||
+            (!g->deg.p && !g->deg.alloc(&o->al, n)))
             fail(HOMLN_ENOMEM, "closeness outputs");
         if (!g->bfs_ready || g->bfs.relabeled != (h->tuning.relabel != 0)) prep.push_back(it);
         jobs.push_back(BfsJob{&g->bfs, g->F.p, g->R.p});
@@ -362,7 +363,11 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
     // that owns it, which need not be ordered after the launches that read it: wait for the
     // device first (a rare path).
     bool rebuild = false;
-    for (const auto &it : prep) rebuild |= it.second->bfs_ready;
+    for (const auto &it : prep) {
+        rebuild |= it.second->bfs_ready;
+        if (it.second->bfs_ready && it.second->graph_refs > 0)
+            fail(HOMLN_EBUSY, "a captured graph uses this BFS graph; destroy it before changing the relabelling");
+    }
     if (rebuild) {
         HCUDA(cudaDeviceSynchronize());
         for (const auto &it : prep) {
@@ -395,6 +400,36 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
         HCUDA(cudaStreamWaitEvent(h->stream, e, 0));
         cudaEventDestroy(e);
     }
+    return jobs;
+}
+
+// The other handles' streams of `todo` wait for everything queued so far on h's stream.
+void order_after(homln_t h, const Items &todo) {
+    std::vector<homln_t> others;
+    for (const auto &it : todo)
+        if (it.first != h && it.first->stream != h->stream &&
+            std::find(others.begin(), others.end(), it.first) == others.end())
+            others.push_back(it.first);
+    for (homln_t o : others) {
+        cudaEvent_t e;
+        HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        HCUDA(cudaEventRecord(e, h->stream));
+        HCUDA(cudaStreamWaitEvent(o->stream, e, 0));
+        cudaEventDestroy(e);
+    }
+}
+
+// Psi for every (handle, graph) item not analysed yet, in one persistent BFS launch on the
+// stream of `h` (the other handles' streams are ordered around it with events). Each graph's
+// outputs are allocated through its own handle.
+void analyse_items(homln_t h, const Items &items) {
+    Items todo;
+    for (const auto &it : items)
+        if (!it.second->analysed &&
+            std::find_if(todo.begin(), todo.end(), [&](const auto &x) { return x.second == it.second; }) == todo.end())
+            todo.push_back(it);
+    if (todo.empty()) return;
+    std::vector<BfsJob> jobs = prepare_items(h, todo);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling) {
         HCUDA(cudaEventCreate(&e0));
@@ -424,13 +459,7 @@ void analyse_items(homln_t h, const std::vector<std::pair<homln_t, GraphState *>
                            h->stream);
         g->analysed = true;
     }
-    for (homln_t o : others) {  // and the other streams wait for the results
-        cudaEvent_t e;
-        HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        HCUDA(cudaEventRecord(e, h->stream));
-        HCUDA(cudaStreamWaitEvent(o->stream, e, 0));
-        cudaEventDestroy(e);
-    }
+    order_after(h, todo);  // and the other streams wait for the results
 }
 
 void analyse_many(homln_t h, const std::vector<GraphState *> &gs) {
@@ -629,6 +658,7 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
 homln_status homln_destroy(homln_t h) {
     if (!h) return HOMLN_OK;
     API_BEGIN
+    if (h->live_graphs > 0) fail(HOMLN_EBUSY, "a captured graph still uses this handle; destroy it first");
     cudaSetDevice(h->device);
     cudaStream_t s = h->stream;
     // buffers owned by a lane are freed on it: after everything queued on the handle's stream
@@ -712,6 +742,123 @@ homln_status homln_batch_analyse(homln_t *nets, int32_t count, const uint64_t *m
         if (with_and) items.push_back({nets[i], &and_graph(nets[i], masks[i])});
     }
     analyse_items(h, items);
+    API_END
+}
+
+}  // extern "C"
+
+// A captured analysis: the plan's buffers, the graphs it writes, and the instantiated graph.
+struct homln_graph_s {
+    homln_t h = nullptr;  // the launching handle (its stream, tuning and error word)
+    Items items;
+    std::vector<homln_t> handles;
+    BfsPlan *plan = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~homln_graph_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        bfs_plan_destroy(plan);
+        for (auto &it : items) it.second->graph_refs -= 1;
+        for (homln_t o : handles) o->live_graphs -= 1;
+    }
+};
+
+extern "C" {
+
+homln_status homln_graph_capture(homln_t *nets, int32_t count, const uint64_t *masks, int32_t with_and,
+                                 homln_graph_t *out) {
+    API_BEGIN
+    if (!nets || !masks || count < 1 || !out) fail(HOMLN_EINVAL, "nets, masks, count >= 1 and out are required");
+    for (int32_t i = 0; i < count; ++i)
+        if (!nets[i]) fail(HOMLN_EINVAL, "null handle in nets");
+    homln_t h = nets[0];
+    for (int32_t i = 1; i < count; ++i)
+        if (nets[i]->device != h->device) fail(HOMLN_EINVAL, "all handles must live on one device");
+    if (h->tuning.schedule == 1) fail(HOMLN_EINVAL, "the plain schedule cannot be captured (the host drives it)");
+    if (h->instrument) fail(HOMLN_EINVAL, "an instrumented handle cannot be captured");
+    use_device(h);
+    Items items;
+    for (int32_t i = 0; i < count; ++i) {
+        std::vector<GraphState *> gs;
+        for (int l : mask_layers(nets[i], masks[i])) gs.push_back(nets[i]->layers[l].get());
+        if (with_and) gs.push_back(&and_graph(nets[i], masks[i]));
+        for (GraphState *g : gs)
+            if (std::find_if(items.begin(), items.end(), [&](const auto &x) { return x.second == g; }) == items.end())
+                items.push_back({nets[i], g});
+    }
+    auto gr = std::make_unique<homln_graph_s>();
+    gr->h = h;
+    std::vector<BfsJob> jobs = prepare_items(h, items);
+    gr->plan = bfs_plan_create(jobs, h->tuning, h->err.p, &h->al, h->stream, false);
+    for (int32_t i = 0; i < count; ++i) HCUDA(cudaStreamSynchronize(nets[i]->stream));  // preparation done
+    // captured on a private stream (the handle's may be the legacy default stream, which cannot
+    // be captured); replays run on the handle's stream
+    struct CaptureStream {
+        cudaStream_t s = nullptr;
+        ~CaptureStream() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } cs;
+    HCUDA(cudaStreamCreateWithFlags(&cs.s, cudaStreamNonBlocking));
+    HCUDA(cudaStreamBeginCapture(cs.s, cudaStreamCaptureModeThreadLocal));
+    try {
+        bfs_plan_run(gr->plan, cs.s, nullptr, nullptr);
+        for (const auto &it : items) {
+            GraphState *g = it.second;
+            closeness_finalize(it.first->n, in_csr(it.first, *g).rowptr.p, g->F.p, g->R.p, g->cc.p, g->sumdist.p,
+                               g->deg.p, cs.s);
+        }
+    } catch (...) {
+        cudaGraph_t partial = nullptr;
+        cudaStreamEndCapture(cs.s, &partial);
+        if (partial) cudaGraphDestroy(partial);
+        cudaGetLastError();
+        throw;
+    }
+    HCUDA(cudaStreamEndCapture(cs.s, &gr->graph));
+    HCUDA(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
+    gr->items = items;
+    for (auto &it : gr->items) it.second->graph_refs += 1;
+    for (const auto &it : items)
+        if (std::find(gr->handles.begin(), gr->handles.end(), it.first) == gr->handles.end()) {
+            gr->handles.push_back(it.first);
+            it.first->live_graphs += 1;
+        }
+    *out = gr.release();
+    API_END
+}
+
+homln_status homln_graph_launch(homln_graph_t g) {
+    API_BEGIN
+    if (!g) fail(HOMLN_EINVAL, "null graph");
+    homln_t h = g->h;
+    use_device(h);
+    // the other handles' streams are ordered before and after the replay on h's stream
+    for (homln_t o : g->handles)
+        if (o != h && o->stream != h->stream) {
+            cudaEvent_t e;
+            HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            HCUDA(cudaEventRecord(e, o->stream));
+            HCUDA(cudaStreamWaitEvent(h->stream, e, 0));
+            cudaEventDestroy(e);
+        }
+    HCUDA(cudaGraphLaunch(g->exec, h->stream));
+    h->bfs_launches += 1;
+    for (auto &it : g->items) {
+        it.second->analysed = true;
+        it.second->selections.clear();
+    }
+    order_after(h, g->items);
+    API_END
+}
+
+homln_status homln_graph_destroy(homln_graph_t g) {
+    if (!g) return HOMLN_OK;
+    API_BEGIN
+    cudaSetDevice(g->h->device);
+    for (homln_t o : g->handles) HCUDA(cudaStreamSynchronize(o->stream));
+    delete g;
     API_END
 }
 

@@ -290,6 +290,18 @@ struct BfsGraph {
 // g_in: the in-edge CSR of a directed graph (nullptr when undirected).
 void bfs_prepare(const Csr &g, const Csr *g_in, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s);
 
+// A BFS over a job list with everything allocated once (msbfs.cu): bfs_plan_run enqueues one
+// complete analysis without allocating or copying from the host (capturable in a CUDA graph,
+// except the plain schedule and instrumented plans).
+struct BfsPlan;
+struct BfsJob;
+BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al,
+                         cudaStream_t s, bool stats);
+void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+void bfs_plan_stats(BfsPlan *p, BfsStats *stats, cudaStream_t s);
+bool bfs_plan_capturable(const BfsPlan *p);
+void bfs_plan_destroy(BfsPlan *p);
+
 struct BfsJob {
     const BfsGraph *g;
     uint64_t *F;  // outputs in the original vertex order

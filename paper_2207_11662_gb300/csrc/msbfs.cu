@@ -23,6 +23,8 @@
 // independently, so one team's wait overlaps another team's work.
 #include "common.cuh"
 
+#include <memory>
+
 #include <algorithm>
 
 namespace homln {
@@ -988,21 +990,51 @@ int msbfs_pick_words(int32_t n) {
     return W;
 }
 
-void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
-                 BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
-    if (jobs.empty()) return;
+// Everything one BFS over a job list needs, allocated once: the graph descriptors, the
+// relabelled graphs' F/R scratch and the teams' state. bfs_plan_run enqueues one complete
+// analysis (zeroing, launches, scatter-back) without allocating or copying from the host, so
+// it can be captured in a CUDA graph and replayed.
+struct BfsPlan {
+    std::vector<BfsJob> jobs;
+    BfsTuning t;
+    bool plain = false, stats = false;
+    int W = 8, nteams = 1, threads = 512, grid = 0, nsm = 0, per_sm = 0;
+    BfsKernel kern = nullptr;
+    PhaseKernel pkern = nullptr;
+    std::vector<GraphDesc> desc;
+    int32_t tiles = 0, maxn = 0;
+    std::vector<DBuf<uint64_t>> Fi;
+    std::vector<DBuf<uint32_t>> Ri;
+    DBuf<uint64_t> state;
+    DBuf<uint8_t> quiet;
+    DBuf<unsigned long long> ctr, st;
+    DBuf<uint32_t> barmem;
+    DBuf<int32_t> queue;
+    DBuf<GraphDesc> d_desc;
+    size_t bar_words = 0;
+    TeamArgs A{};
+};
+
+BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al,
+                         cudaStream_t s, bool stats) {
+    if (jobs.empty()) return nullptr;
     int32_t maxn = 0;
     for (const BfsJob &j : jobs) maxn = std::max(maxn, j.g->csr.n);
-    if (maxn <= 0) return;
+    if (maxn <= 0) return nullptr;
     const int threads = t.threads > 0 ? t.threads : 512;
     if (threads % 32 != 0 || threads > 512 || threads < 64) fail(HOMLN_EINVAL, "threads must be 64..512, multiple of 32");
-
-    const bool plain = t.schedule == 1;
+    std::unique_ptr<BfsPlan> p(new BfsPlan);
+    p->jobs = jobs;
+    p->t = t;
+    p->stats = stats;
+    p->threads = threads;
+    p->maxn = maxn;
+    const bool plain = p->plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
     // Defaults, measured on GB300: 8 words per node (512 sources per tile), 16 teams.
     // The plain schedule (one team, the host driving every level) takes the widest tile the
     // budget allows, which needs the fewest launches and host round trips.
-    int W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn) : std::min(8, msbfs_pick_words(maxn));
+    const int W = p->W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn) : std::min(8, msbfs_pick_words(maxn));
     int nteams = 1;
     if (!plain) {
         if (t.teams > 0) {
@@ -1015,30 +1047,31 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
             if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
         }
     }
-    const int T = W >= 2 ? W / 2 : 1;
-
-    BfsKernel kern = kernel_for(W, stats != nullptr);
+    p->kern = kernel_for(W, stats);
     int dev = 0, nsm = 0, coop = 0, per_sm = 0;
     HCUDA(cudaGetDevice(&dev));
     HCUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     HCUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) fail(HOMLN_ECUDA, "device does not support cooperative launch");
-    PhaseKernel pkern = plain ? phase_kernel_for(W, stats != nullptr) : nullptr;
-    HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    p->pkern = plain ? phase_kernel_for(W, stats) : nullptr;
+    HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
-    const int grid = nsm * per_sm;
+    const int grid = p->grid = nsm * per_sm;
     if (nteams > grid) nteams = grid;
+    p->nteams = nteams;
+    p->nsm = nsm;
+    p->per_sm = per_sm;
 
     // graph descriptors; relabelled graphs accumulate into scratch and are scattered back after
     const size_t ng = jobs.size();
-    std::vector<DBuf<uint64_t>> Fi(ng);
-    std::vector<DBuf<uint32_t>> Ri(ng);
-    std::vector<GraphDesc> desc(ng);
+    p->Fi.resize(ng);
+    p->Ri.resize(ng);
+    p->desc.resize(ng);
     int32_t tile = 0;
     for (size_t i = 0; i < ng; ++i) {
         const BfsGraph &G = *jobs[i].g;
-        GraphDesc &d = desc[i];
+        GraphDesc &d = p->desc[i];
         d.n = G.csr.n;
         d.nbatches = (int32_t)ceil_div(d.n, 64 * W);
         d.tile0 = tile;
@@ -1049,89 +1082,101 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
         d.prow = G.directed ? G.csr_in.rowptr.p : G.csr.rowptr.p;
         d.pcol = G.directed ? G.csr_in.col.p : G.csr.col.p;
         if (G.relabeled) {
-            if (!Fi[i].alloc(al, d.n) || !Ri[i].alloc(al, d.n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
-            d.F = Fi[i].p;
-            d.R = Ri[i].p;
+            if (!p->Fi[i].alloc(al, d.n) || !p->Ri[i].alloc(al, d.n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
+            d.F = p->Fi[i].p;
+            d.R = p->Ri[i].p;
         } else {
             d.F = jobs[i].F;
             d.R = jobs[i].R;
         }
-        HCUDA(cudaMemsetAsync(d.F, 0, (size_t)d.n * sizeof(uint64_t), s));
-        HCUDA(cudaMemsetAsync(d.R, 0, (size_t)d.n * sizeof(uint32_t), s));
     }
+    p->tiles = tile;
 
     const size_t words = (size_t)maxn * W * nteams;
-    DBuf<uint64_t> state;
-    DBuf<uint8_t> quiet;
-    DBuf<unsigned long long> ctr, st;
-    DBuf<uint32_t> barmem;
-    DBuf<int32_t> queue;
-    DBuf<GraphDesc> d_desc;
-    const size_t bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
-    if (!state.alloc(al, 3 * words) || !quiet.alloc(al, 3 * (size_t)maxn * nteams) || !ctr.alloc(al, 16 * nteams) ||
-        !barmem.alloc(al, bar_words) || !queue.alloc(al, 1) || !d_desc.alloc(al, ng))
+    p->bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
+    if (!p->state.alloc(al, 3 * words) || !p->quiet.alloc(al, 3 * (size_t)maxn * nteams) ||
+        !p->ctr.alloc(al, 16 * nteams) || !p->barmem.alloc(al, p->bar_words) || !p->queue.alloc(al, 1) ||
+        !p->d_desc.alloc(al, ng))
         fail(HOMLN_ENOMEM, "bfs state");
-    if (stats && !st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
-    HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
-    HCUDA(cudaMemsetAsync(barmem.p, 0, bar_words * sizeof(uint32_t), s));
-    HCUDA(cudaMemsetAsync(queue.p, 0, sizeof(int32_t), s));
-    HCUDA(cudaMemcpyAsync(d_desc.p, desc.data(), ng * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
-    if (stats) HCUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
+    if (stats && !p->st.alloc(al, ST_N)) fail(HOMLN_ENOMEM, "bfs stats");
+    HCUDA(cudaMemcpyAsync(p->d_desc.p, p->desc.data(), ng * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
 
-    TeamArgs A{};
-    A.graphs = d_desc.p;
+    TeamArgs &A = p->A;
+    A.graphs = p->d_desc.p;
     A.ngraphs = (int32_t)ng;
     A.ntiles = tile;
     A.nteams = nteams;
     A.push_alpha = t.push_alpha > 0 ? t.push_alpha : 16;
     A.maxn = maxn;
-    A.state = state.p;
-    A.quiet = quiet.p;
-    A.fresh = quiet.p + (size_t)maxn * nteams;
-    A.pushed = quiet.p + 2 * (size_t)maxn * nteams;
-    A.ctr = ctr.p;
-    A.bar = barmem.p;
-    A.grid_bar = barmem.p + 32 * (size_t)nteams;
-    A.sm_slots = barmem.p + 32 * (size_t)nteams + 32;
+    A.state = p->state.p;
+    A.quiet = p->quiet.p;
+    A.fresh = p->quiet.p + (size_t)maxn * nteams;
+    A.pushed = p->quiet.p + 2 * (size_t)maxn * nteams;
+    A.ctr = p->ctr.p;
+    A.bar = p->barmem.p;
+    A.grid_bar = p->barmem.p + 32 * (size_t)nteams;
+    A.sm_slots = p->barmem.p + 32 * (size_t)nteams + 32;
     A.nsm = nsm;
     A.per_sm = per_sm;
     A.team_mix = t.team_mix;
-    A.queue = queue.p;
+    A.queue = p->queue.p;
     A.err = d_err;
     A.atomic_fr = nteams > 1 ? 1 : 0;
-    A.stats = stats ? st.p : nullptr;
+    A.stats = stats ? p->st.p : nullptr;
     A.wait_ns = (uint64_t)t.wait_limit_ms * 1000000ull;
     A.phantom = t.phantom;
+    return p.release();
+}
+
+void bfs_plan_destroy(BfsPlan *p) { delete p; }
+
+bool bfs_plan_capturable(const BfsPlan *p) { return p && !p->plain && !p->stats; }
+
+void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    if (!p) return;
+    const size_t ng = p->jobs.size();
+    const int32_t tile = p->tiles;
+    const int W = p->W, grid = p->grid, threads = p->threads, nteams = p->nteams;
+    for (size_t i = 0; i < ng; ++i) {
+        HCUDA(cudaMemsetAsync(p->desc[i].F, 0, (size_t)p->desc[i].n * sizeof(uint64_t), s));
+        HCUDA(cudaMemsetAsync(p->desc[i].R, 0, (size_t)p->desc[i].n * sizeof(uint32_t), s));
+    }
+    HCUDA(cudaMemsetAsync(p->ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
+    HCUDA(cudaMemsetAsync(p->barmem.p, 0, p->bar_words * sizeof(uint32_t), s));
+    HCUDA(cudaMemsetAsync(p->queue.p, 0, sizeof(int32_t), s));
+    if (p->stats) HCUDA(cudaMemsetAsync(p->st.p, 0, ST_N * sizeof(unsigned long long), s));
+    TeamArgs A = p->A;
     void *args[] = {&A};
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
-    if (!plain) {
+    if (!p->plain) {
         // max_tiles: the tiles go out in several launches of at most that many, so that work of
         // other streams (a higher-priority one, say) can run in between
-        const int32_t chunk = t.max_tiles > 0 ? t.max_tiles : tile;
+        const int32_t chunk = p->t.max_tiles > 0 ? p->t.max_tiles : tile;
         for (int32_t c0 = 0; c0 < tile; c0 += chunk) {
             if (c0 > 0) {  // fresh barriers, counters and team formation; the queue resumes at c0
-                HCUDA(cudaMemsetAsync(ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
-                HCUDA(cudaMemsetAsync(barmem.p, 0, bar_words * sizeof(uint32_t), s));
-                launch(k_set_i32, 1, 1, 0, s, queue.p, c0);
+                HCUDA(cudaMemsetAsync(p->ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
+                HCUDA(cudaMemsetAsync(p->barmem.p, 0, p->bar_words * sizeof(uint32_t), s));
+                launch(k_set_i32, 1, 1, 0, s, p->queue.p, c0);
             }
             A.ntiles = (int32_t)std::min<int64_t>(tile, (int64_t)c0 + chunk);
             g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-            HCUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(threads), args, 0, s));
+            HCUDA(cudaLaunchCooperativeKernel((const void *)p->kern, dim3(grid), dim3(threads), args, 0, s));
         }
     } else {
         // plain schedule: one launch per phase, the host reads the level counters after every level
+        const PhaseKernel pkern = p->pkern;
         uint32_t ps = 0;
         for (size_t gi = 0; gi < ng; ++gi) {
-            for (int32_t b = 0; b < desc[gi].nbatches; ++b) {
-                const int32_t s0 = b * 64 * W, ns = std::min(64 * W, desc[gi].n - s0);
+            for (int32_t b = 0; b < p->desc[gi].nbatches; ++b) {
+                const int32_t s0 = b * 64 * W, ns = std::min(64 * W, p->desc[gi].n - s0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START_PUSH, s0, ns, 0, ps, 0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, 1, ps, 0);
                 ++ps;
                 int32_t cur_a = 1;
-                for (int32_t level = 2; level <= desc[gi].n + 1; ++level) {
+                for (int32_t level = 2; level <= p->desc[gi].n + 1; ++level) {
                     unsigned long long h3[3];
-                    HCUDA(cudaMemcpyAsync(h3, ctr.p + 4 * ((ps - 1) % 3), sizeof(h3), cudaMemcpyDeviceToHost, s));
+                    HCUDA(cudaMemcpyAsync(h3, p->ctr.p + 4 * ((ps - 1) % 3), sizeof(h3), cudaMemcpyDeviceToHost, s));
                     HCUDA(cudaStreamSynchronize(s));
                     if (h3[0] == 0) break;
                     if ((unsigned long long)A.push_alpha * h3[1] < h3[2]) {
@@ -1149,11 +1194,18 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
     }
     if (ev_stop) HCUDA(cudaEventRecord(ev_stop, s));
     for (size_t i = 0; i < ng; ++i)
-        if (jobs[i].g->relabeled)
-            launch(k_scatter_back, (unsigned)ceil_div(desc[i].n, 256), 256, 0, s, desc[i].n, jobs[i].g->perm.p,
-                   (const uint64_t *)Fi[i].p, (const uint32_t *)Ri[i].p, jobs[i].F, jobs[i].R);
+        if (p->jobs[i].g->relabeled)
+            launch(k_scatter_back, (unsigned)ceil_div(p->desc[i].n, 256), 256, 0, s, p->desc[i].n,
+                   p->jobs[i].g->perm.p, (const uint64_t *)p->Fi[i].p, (const uint32_t *)p->Ri[i].p, p->jobs[i].F,
+                   p->jobs[i].R);
     HCUDA(cudaGetLastError());
-    if (stats) {
+}
+
+void bfs_plan_stats(BfsPlan *p, BfsStats *stats, cudaStream_t s) {
+    if (!p || !p->stats || !stats) return;
+    const int W = p->W, nteams = p->nteams;
+    const auto &st = p->st;
+    {
         unsigned long long h[ST_N];
         HCUDA(cudaMemcpyAsync(h, st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
         HCUDA(cudaStreamSynchronize(s));
@@ -1170,6 +1222,13 @@ void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d
         stats->words_per_node = W;
         stats->teams = nteams;
     }
+}
+
+void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
+                 BfsStats *stats, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    std::unique_ptr<BfsPlan> p(bfs_plan_create(jobs, t, d_err, al, s, stats != nullptr));
+    bfs_plan_run(p.get(), s, ev_start, ev_stop);
+    bfs_plan_stats(p.get(), stats, s);
 }
 
 static void copy_csr(const Csr &g, Csr &out, Alloc *al, cudaStream_t s) {

@@ -34,7 +34,7 @@ EXPORTS = [
     "homln_get_profile", "homln_reset_profile", "homln_kernel_launches", "homln_sync", "homln_last_error",
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
     "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness", "homln_export_partials",
-    "homln_import_partials",
+    "homln_import_partials", "homln_graph_capture", "homln_graph_launch", "homln_graph_destroy",
 ]
 
 
@@ -117,6 +117,9 @@ def _load():
         "homln_subset_sweep": (S, [c_void_p, c_int32, POINTER(homln_select), c_int32, POINTER(homln_subset_result),
                                    c_int32, POINTER(c_int32)]),
         "homln_export_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p]),
+        "homln_graph_capture": (S, [POINTER(c_void_p), c_int32, POINTER(c_uint64), c_int32, POINTER(c_void_p)]),
+        "homln_graph_launch": (S, [c_void_p]),
+        "homln_graph_destroy": (S, [c_void_p]),
         "homln_import_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p]),
         "homln_last_error": (c_char_p, []),
         "homln_version": (c_char_p, []),
@@ -249,6 +252,24 @@ def homln_or_aggregate(h, layer_mask: int, capacity: int = 0, or_src=None, or_ds
 
 def homln_or_closeness(h, layer_mask: int, farness=None, reach=None, cc=None) -> None:
     _check(lib.homln_or_closeness(h, int(layer_mask), ptr(farness), ptr(reach), ptr(cc)), "homln_or_closeness")
+
+
+def homln_graph_capture(handles, masks, with_and: bool = True) -> int:
+    """Capture the batched analysis of `handles` into a replayable CUDA graph (opaque handle)."""
+    n = len(handles)
+    hs = (c_void_p * n)(*handles)
+    ms = (c_uint64 * n)(*[int(m) for m in masks])
+    out = c_void_p()
+    _check(lib.homln_graph_capture(hs, n, ms, int(bool(with_and)), ctypes.byref(out)), "homln_graph_capture")
+    return out.value
+
+
+def homln_graph_launch(g) -> None:
+    _check(lib.homln_graph_launch(g), "homln_graph_launch")
+
+
+def homln_graph_destroy(g) -> None:
+    _check(lib.homln_graph_destroy(g), "homln_graph_destroy")
 
 
 def homln_export_partials(h, which: int, layer_mask: int, farness, reach, degree=None) -> None:

@@ -630,3 +630,29 @@ def test_tiles_split_over_several_launches(H, max_tiles):
     net = synth.homln_small_overlap(2100, 6.0, 3, 0.4, 93)
     sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
     full_parity(H, net, sel, tuning=dict(max_tiles_per_launch=max_tiles, words_per_node=2), heuristics=(2,))
+
+
+def test_captured_graph_replays_the_batched_analysis(H):
+    """homln_graph_capture: replays recompute every captured graph exactly; handles in use by a
+    graph cannot be destroyed; after the graph is gone they can."""
+    import torch
+    nets = synth.homln_batch(count=5, seed=101, n_range=(300, 2500), layer_range=(2, 4))
+    gs = [H.Network(net.n, to_dev(net.layers)) for net in nets]
+    masks = [(1 << net.n_layers) - 1 for net in nets]
+    graph = H.homln_graph_capture([g.h for g in gs], masks, True)
+    refs = [O.OracleHoMLN(net.n, net.layers, threads=8) for net in nets]
+    for rep in range(2):
+        for g in gs:
+            H.homln_invalidate(g.h)
+        H.homln_graph_launch(graph)
+        for g, net, mask, ref in zip(gs, nets, masks, refs):
+            for i in range(net.n_layers):
+                check_graph(*g.layer_closeness(i), ref.layer(i))
+            check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+    with pytest.raises(H.HomlnError) as e:
+        H.homln_destroy(gs[1].h)
+    assert e.value.code == H.HOMLN_EBUSY
+    H.homln_graph_destroy(graph)
+    for g in gs:
+        g.close()
+    torch.cuda.synchronize()
