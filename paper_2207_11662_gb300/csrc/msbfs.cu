@@ -1,31 +1,32 @@
 // All-sources BFS distance sums with a bitset multi-source BFS (MS-BFS).
 //
 // What it computes (Section 4: closeness by BFS from every vertex; Section 5.1:
-// the per-node distance sums CC1/CC2 keep): for every vertex v of an undirected
-// unweighted graph,
-//     F[v] = sum over vertices u reachable from v of d(v, u),
-//     R[v] = number of vertices reachable from v, v excluded.
+// the per-node distance sums CC1/CC2 keep): for every vertex v of an unweighted
+// graph,
+//     F[v] = sum over vertices u that v reaches (undirected) or that reach v
+//            (directed: in-closeness) of the hop distance,
+//     R[v] = number of those vertices, v excluded.
 //
 // How: sources are processed in batches of S = 64*W. Every vertex carries S-bit
-// words -- seen, frontier, next -- one bit per source of the batch. A level
-// either pulls (bottom-up: next[v] = OR of frontier[u] over neighbours u, minus
-// seen[v]) or pushes (top-down: every frontier vertex ORs its word into its
-// neighbours' accumulators, then a sweep keeps the bits not yet seen). Because
-// the graph is undirected, d(s, v) = d(v, s): a bit of source s that first
-// reaches v at level l adds l to F[v] directly, so no per-source scatter is
-// needed -- F[v] += l * popc(new[v]), R[v] += popc(new[v]).
+// words -- seen and two frontier buffers -- one bit per source of the batch. A
+// level either pulls (bottom-up: the new bits of v are the OR of its
+// (in-)neighbours' frontier words, minus seen[v]) or pushes (top-down: every
+// vertex with new bits on the previous level ORs its words into its
+// (out-)neighbours' next frontier words, then a sweep keeps the bits not yet
+// seen). A bit of source s that first reaches v at level l means d(s, v) = l,
+// which undirected is d(v, s): F[v] += l * popc(new[v]), R[v] += popc(new[v]),
+// with no per-source scatter; directed, the same sum is v's in-farness.
 //
 // Scheduling: one persistent cooperative launch covers every (graph, batch)
 // tile of one or many graphs (the layers of a HoMLN and their AND aggregate, or
-// many HoMLNs). The grid is split into teams of blocks, interleaved over the
-// SMs; a team pops the next tile from a device queue and runs its levels,
-// separated by a bounded barrier over the team's blocks only. Teams progress
-// independently, so one team's wait overlaps another team's work.
+// many HoMLNs). The grid is split into teams of blocks; a team pops the next
+// tile from a device queue and runs its levels, separated by a bounded barrier
+// over the team's blocks only. Teams progress independently, so one team's wait
+// overlaps another team's work.
 #include "common.cuh"
 
-#include <memory>
-
 #include <algorithm>
+#include <memory>
 
 namespace homln {
 
@@ -1203,25 +1204,21 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
 
 void bfs_plan_stats(BfsPlan *p, BfsStats *stats, cudaStream_t s) {
     if (!p || !p->stats || !stats) return;
-    const int W = p->W, nteams = p->nteams;
-    const auto &st = p->st;
-    {
-        unsigned long long h[ST_N];
-        HCUDA(cudaMemcpyAsync(h, st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-        HCUDA(cudaStreamSynchronize(s));
-        stats->levels += h[ST_LEVELS];
-        stats->pull_levels += h[ST_PULL];
-        stats->push_levels += h[ST_PUSH];
-        stats->group_edges += h[ST_EDGES];
-        stats->lane_words += h[ST_WORDS];
-        stats->push_edges += h[ST_PUSHED];
-        stats->batches += h[ST_BATCHES];
-        stats->push_words += h[ST_PUSHWORDS];
-        stats->bytes += h[ST_BYTES];
-        stats->visits += h[ST_VISITS];
-        stats->words_per_node = W;
-        stats->teams = nteams;
-    }
+    unsigned long long h[ST_N];
+    HCUDA(cudaMemcpyAsync(h, p->st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    HCUDA(cudaStreamSynchronize(s));
+    stats->levels += h[ST_LEVELS];
+    stats->pull_levels += h[ST_PULL];
+    stats->push_levels += h[ST_PUSH];
+    stats->group_edges += h[ST_EDGES];
+    stats->lane_words += h[ST_WORDS];
+    stats->push_edges += h[ST_PUSHED];
+    stats->batches += h[ST_BATCHES];
+    stats->push_words += h[ST_PUSHWORDS];
+    stats->bytes += h[ST_BYTES];
+    stats->visits += h[ST_VISITS];
+    stats->words_per_node = p->W;
+    stats->teams = p->nteams;
 }
 
 void msbfs_multi(const std::vector<BfsJob> &jobs, const BfsTuning &t, int32_t *d_err, Alloc *al, cudaStream_t s,
