@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--teams", type=int, default=0, help="BFS teams (0 = auto)")
     p.add_argument("--team-mix", type=int, default=0, help="1: blocks on one SM join different teams")
+    p.add_argument("--threads", type=int, default=0, help="threads per BFS block (0 = 512)")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -237,6 +238,8 @@ def run_ours(args, rank, world, dist):
         tuning["teams"] = args.teams
     if args.team_mix:
         tuning["team_mix"] = 1
+    if args.threads:
+        tuning["threads"] = args.threads
     sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
     stream = torch.cuda.current_stream(dev)
     dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]

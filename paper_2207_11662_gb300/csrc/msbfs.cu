@@ -248,6 +248,9 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b) {
 #ifndef HOMLN_GATHER_UNROLL
 #define HOMLN_GATHER_UNROLL 4
 #endif
+#ifndef HOMLN_BFS_MAX_THREADS
+#define HOMLN_BFS_MAX_THREADS 512
+#endif
 #ifndef HOMLN_BFS_MIN_BLOCKS
 #define HOMLN_BFS_MIN_BLOCKS 2
 #endif
@@ -769,7 +772,7 @@ __device__ __forceinline__ uint32_t sm_id() {
 }
 
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A) {
+__global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A) {
     PhaseCounters c;
     unsigned long long st[ST_N];
 #pragma unroll
@@ -870,7 +873,7 @@ __global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_msbfs(TeamArgs A)
 enum PhaseKind { PH_START = 0, PH_FINALIZE = 1, PH_PULL = 2, PH_PUSH = 3, PH_START_PUSH = 4 };
 
 template <int W, bool STATS>
-__global__ void __launch_bounds__(512, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
+__global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k_phase(TeamArgs A, int32_t gi, int32_t kind, int32_t s0, int32_t ns,
                                                   int32_t level, uint32_t ps, int32_t cur_is_a) {
     PhaseCounters c;
     unsigned long long st[ST_N];
