@@ -343,6 +343,18 @@ HOMLN_API int64_t homln_kernel_launches(void);
 HOMLN_API homln_status homln_export_partials(homln_t h, int32_t which, uint64_t layer_mask, uint64_t *farness,
                                              uint32_t *reach, int32_t *degree);
 
+/* One shard of the analysis of graph `which` (as in homln_export_partials), for splitting it
+ * over several GPUs or processes: the BFS from the source batches rank, rank + world,
+ * rank + 2 world, ... only (a batch is 64 x words_per_node sources of the graph's BFS order).
+ * farness[n] / reach[n] (uint64 / uint32, host or device) receive the partial sums over those
+ * sources; summed element-wise over rank = 0 .. world-1 (an all-reduce) they are exactly the
+ * graph's farness and reach, which homln_import_partials then takes as its analysis (Section 3
+ * keeps analyses apart from compositions; the sum is exact integer arithmetic). The handle's
+ * cached results are not touched. Errors: EINVAL (rank/world, which, the plain schedule),
+ * ENOMEM, ECUDA, ETIMEOUT. */
+HOMLN_API homln_status homln_shard_partials(homln_t h, int32_t which, uint64_t layer_mask, int32_t rank,
+                                            int32_t world, uint64_t *farness, uint32_t *reach);
+
 /* Resume from a checkpoint: take farness/reach (host or device, n entries each) as the analysis
  * of graph `which` (as in homln_export_partials) of this handle, which must hold the same layers
  * they were computed on; closeness, sumDist and degrees are derived from them and the handle's

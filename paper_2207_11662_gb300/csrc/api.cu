@@ -941,6 +941,33 @@ GraphState &graph_of(homln_t h, int32_t which, uint64_t layer_mask) {
 }
 }  // namespace
 
+homln_status homln_shard_partials(homln_t h, int32_t which, uint64_t layer_mask, int32_t rank, int32_t world,
+                                  uint64_t *farness, uint32_t *reach) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "null handle");
+    if (!farness || !reach) fail(HOMLN_EINVAL, "farness and reach are required");
+    if (world < 1 || world > 65536 || rank < 0 || rank >= world) fail(HOMLN_EINVAL, "need 0 <= rank < world");
+    if (h->tuning.schedule == 1) fail(HOMLN_EINVAL, "sharded partials use the persistent schedule");
+    use_device(h);
+    GraphState &g = graph_of(h, which, layer_mask);
+    // the graph's BFS form, as an analysis would build it; the partial sums go to scratch
+    Items one{{h, &g}};
+    prepare_items(h, one);
+    const int32_t n = h->n;
+    DBuf<uint64_t> F;
+    DBuf<uint32_t> R;
+    if (!F.alloc(&h->al, n) || !R.alloc(&h->al, n)) fail(HOMLN_ENOMEM, "shard partials");
+    BfsTuning t = h->tuning;
+    t.shard_rank = rank;
+    t.shard_world = world;
+    msbfs_multi({BfsJob{&g.bfs, F.p, R.p}}, t, h->err.p, &h->al, h->stream, nullptr, nullptr, nullptr);
+    h->bfs_launches += 1;
+    bool host = put_out(h, farness, F.p, sizeof(uint64_t) * n);
+    host |= put_out(h, reach, R.p, sizeof(uint32_t) * n);
+    if (host) check_device_error(h);
+    API_END
+}
+
 homln_status homln_export_partials(homln_t h, int32_t which, uint64_t layer_mask, uint64_t *farness, uint32_t *reach,
                                    int32_t *degree) {
     API_BEGIN

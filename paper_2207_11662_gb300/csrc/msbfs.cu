@@ -40,9 +40,11 @@ struct GraphDesc {
     uint64_t *F;
     uint32_t *R;
     int32_t n;
-    int32_t nbatches;
+    int32_t nbatches;       // batches of this launch: source batches b0, b0 + bstride, ...
     int32_t tile0;          // index of this graph's first tile
     int32_t by_degree;      // rows are in descending degree order (the hub tiers apply)
+    int32_t b0;             // first source batch (a shard's rank; 0 unsharded)
+    int32_t bstride;        // batch stride (a shard's world size; 1 unsharded)
     int32_t pad;
 };
 
@@ -847,7 +849,7 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
         a.tsize = tsize;
         a.push_alpha = A.push_alpha;
         a.atomic_fr = A.atomic_fr != 0;
-        const int32_t b = t - g.tile0;
+        const int32_t b = g.b0 + (t - g.tile0) * g.bstride;
         const int32_t s0 = b * 64 * W;
         const int32_t ns = min(64 * W, g.n - s0);
         ok = run_batch<W, STATS>(a, fa, fb, tb, s0, ns, ps, c, st);
@@ -1048,6 +1050,7 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
             nteams = std::max(1, std::min(kDefaultTeams, nteams));
             int64_t tiles = 0;  // no more teams than tiles
             for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
+            tiles = ceil_div(tiles, (int64_t)std::max(1, t.shard_world));
             if (tiles < nteams) nteams = (int)std::max<int64_t>(tiles, 1);
         }
     }
@@ -1077,7 +1080,11 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
         const BfsGraph &G = *jobs[i].g;
         GraphDesc &d = p->desc[i];
         d.n = G.csr.n;
-        d.nbatches = (int32_t)ceil_div(d.n, 64 * W);
+        // a shard (rank r of world w) takes the source batches r, r + w, r + 2w, ...
+        const int32_t all = (int32_t)ceil_div(d.n, 64 * W);
+        d.b0 = t.shard_rank;
+        d.bstride = t.shard_world;
+        d.nbatches = all > t.shard_rank ? (all - t.shard_rank + t.shard_world - 1) / t.shard_world : 0;
         d.tile0 = tile;
         tile += d.nbatches;
         d.by_degree = G.relabeled ? 1 : 0;
@@ -1171,7 +1178,8 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
         const PhaseKernel pkern = p->pkern;
         uint32_t ps = 0;
         for (size_t gi = 0; gi < ng; ++gi) {
-            for (int32_t b = 0; b < p->desc[gi].nbatches; ++b) {
+            for (int32_t bi = 0; bi < p->desc[gi].nbatches; ++bi) {
+                const int32_t b = p->desc[gi].b0 + bi * p->desc[gi].bstride;
                 const int32_t s0 = b * 64 * W, ns = std::min(64 * W, p->desc[gi].n - s0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
                 launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START_PUSH, s0, ns, 0, ps, 0);

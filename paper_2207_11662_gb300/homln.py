@@ -35,6 +35,7 @@ EXPORTS = [
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
     "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness", "homln_export_partials",
     "homln_import_partials", "homln_graph_capture", "homln_graph_launch", "homln_graph_destroy",
+    "homln_shard_partials",
 ]
 
 
@@ -119,6 +120,7 @@ def _load():
         "homln_export_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p]),
         "homln_graph_capture": (S, [POINTER(c_void_p), c_int32, POINTER(c_uint64), c_int32, POINTER(c_void_p)]),
         "homln_graph_launch": (S, [c_void_p]),
+        "homln_shard_partials": (S, [c_void_p, c_int32, c_uint64, c_int32, c_int32, c_void_p, c_void_p]),
         "homln_graph_destroy": (S, [c_void_p]),
         "homln_import_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p]),
         "homln_last_error": (c_char_p, []),
@@ -262,6 +264,11 @@ def homln_graph_capture(handles, masks, with_and: bool = True) -> int:
     out = c_void_p()
     _check(lib.homln_graph_capture(hs, n, ms, int(bool(with_and)), ctypes.byref(out)), "homln_graph_capture")
     return out.value
+
+
+def homln_shard_partials(h, which: int, layer_mask: int, rank: int, world: int, farness, reach) -> None:
+    _check(lib.homln_shard_partials(h, int(which), int(layer_mask), int(rank), int(world), ptr(farness), ptr(reach)),
+           "homln_shard_partials")
 
 
 def homln_graph_launch(g) -> None:
@@ -424,6 +431,12 @@ class Network:
 
     def accuracy(self, pred, truth) -> dict:
         return homln_accuracy(self.h, pred, int(pred.shape[0]), truth, int(truth.shape[0]))
+
+    def shard_partials(self, which: int, mask: int, rank: int, world: int):
+        """Partial farness/reach of graph `which` from the source batches of shard rank/world."""
+        F, R = self._empty(self.n, self.torch.int64), self._empty(self.n, self.torch.int32)
+        homln_shard_partials(self.h, which, mask, rank, world, F, R)
+        return F[:self.n], R[:self.n]
 
     def save_partials(self, path: str, masks=()) -> None:
         """Checkpoint the Psi results of every layer and of the AND graphs of `masks` (host .npz)."""

@@ -656,3 +656,31 @@ def test_captured_graph_replays_the_batched_analysis(H):
     for g in gs:
         g.close()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("world", [1, 3, 5])
+def test_sharded_partials_sum_to_the_analysis(H, world):
+    """homln_shard_partials: the ranks' partial sums add up to the exact farness/reach (ranks run
+    one after another on this GPU); imported into a fresh handle they give identical results."""
+    import torch
+    net = synth.homln_small_overlap(2700, 6.0, 3, 0.4, 57)
+    ref = O.OracleHoMLN(net.n, net.layers, threads=8)
+    sel, osel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0)
+    a = H.Network(net.n, to_dev(net.layers), tuning=dict(words_per_node=2))
+    b = H.Network(net.n, to_dev(net.layers))
+    for which, mask, want in [(0, 0, ref.layer(0)), (1, 0, ref.layer(1)), (2, 0, ref.layer(2)),
+                              (-1, 7, ref.and_graph(7))]:
+        F = torch.zeros(net.n, dtype=torch.int64, device="cuda")
+        R = torch.zeros(net.n, dtype=torch.int32, device="cuda")
+        for rank in range(world):
+            f, r = a.shard_partials(which, mask, rank, world)
+            F += f
+            R += r
+        assert np.array_equal(u64(F), want["F"]) and np.array_equal(R.cpu().numpy().astype(np.uint32), want["R"])
+        H.homln_import_partials(b.h, which, mask, F, R)
+    for i in range(3):
+        check_graph(*b.layer_closeness(i), ref.layer(i))
+    assert b.compose(7, 2, sel).cpu().numpy().tolist() == ref.compose(7, 2, osel).tolist()
+    assert b.topk(-1, 7, sel).cpu().numpy().tolist() == ref.topk(-1, 7, osel).tolist()
+    a.close()
+    b.close()
