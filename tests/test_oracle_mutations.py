@@ -68,9 +68,36 @@ def _and_union(n, layer_keys):  # OR instead of AND
     return out
 
 
+def _or_intersection(n, layer_keys):  # AND instead of OR
+    out = layer_keys[0]
+    for k in layer_keys[1:]:
+        out = np.intersect1d(out, k)
+    return out
+
+
+_orig_arc_csr = O.arc_csr
+
+
+def _arc_csr_out_edges(n, keys, reverse=False):  # out-closeness: the in-edge CSR is never built
+    return _orig_arc_csr(n, keys, reverse=False)
+
+
+_orig_arc_keys = O.arc_keys
+
+
+def _arc_keys_symmetrised(n, src, dst):  # arcs made undirected (reverse arc added)
+    return np.union1d(_orig_arc_keys(n, src, dst), _orig_arc_keys(n, dst, src))
+
+
+def _directed_fw():
+    for seed in range(5):
+        P.test_directed_floyd_warshall(seed)
+
+
 PINS = [P.test_empty_graph, P.test_disjoint_components_wf_and_sumdist, P.test_hand_two_layer_example,
         P.test_fig5_cc2_example, P.test_cc2_subset_layers_equals_ground_truth, P.test_selection_special_cases,
-        P.test_accuracy_metrics, P.test_and_aggregation_invariants, P.test_cc2_single_layer_is_sumdist_ranking]
+        P.test_accuracy_metrics, P.test_and_aggregation_invariants, P.test_cc2_single_layer_is_sumdist_ranking,
+        P.test_directed_path_and_cycle_closed_forms, _directed_fw, P.test_directed_aggregates_are_arc_sets]
 
 
 @pytest.mark.parametrize("name,fn", [
@@ -82,6 +109,9 @@ PINS = [P.test_empty_graph, P.test_disjoint_components_wf_and_sumdist, P.test_ha
     ("degrees", _degrees_plus_one),
     ("accuracy", _accuracy_swapped),
     ("and_keys", _and_union),
+    ("or_keys", _or_intersection),
+    ("arc_csr", _arc_csr_out_edges),
+    ("arc_keys", _arc_keys_symmetrised),
 ])
 def test_mutant_is_caught(monkeypatch, name, fn):
     monkeypatch.setattr(O, name, fn)
