@@ -218,6 +218,13 @@ HOMLN_API homln_status homln_graph_launch(homln_graph_t g);
 /* Wait for the graph's replays and release it. NULL is a no-op. */
 HOMLN_API homln_status homln_graph_destroy(homln_graph_t g);
 
+/* The batched analysis in one call: every layer of every handle and the AND graph of all its
+ * layers (homln_batch_analyse with full masks), ordered after the work queued on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream), with `stream` ordered after the results.
+ * For repeated runs, homln_graph_capture holds the same analysis as a CUDA graph.
+ * Errors: as homln_batch_analyse. */
+HOMLN_API homln_status homln_batch_closeness(homln_t *nets, int32_t count, void *stream);
+
 /* Boolean AND aggregation of the layers in `layer_mask` (Section 3.1, Section 4 ground truth):
  * an edge is kept iff it is present in every selected layer. The AND graph is built
  * once per mask and cached. Edges are written as pairs u < v in ascending (u, v) order.

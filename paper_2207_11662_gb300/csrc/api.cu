@@ -745,6 +745,34 @@ homln_status homln_batch_analyse(homln_t *nets, int32_t count, const uint64_t *m
     API_END
 }
 
+homln_status homln_batch_closeness(homln_t *nets, int32_t count, void *stream) {
+    API_BEGIN
+    if (!nets || count < 1) fail(HOMLN_EINVAL, "nets and count >= 1 are required");
+    std::vector<uint64_t> masks(count);
+    for (int32_t i = 0; i < count; ++i) {
+        if (!nets[i]) fail(HOMLN_EINVAL, "null handle in nets");
+        masks[i] = nets[i]->L >= 64 ? ~0ull : (1ull << nets[i]->L) - 1;
+    }
+    homln_t h = nets[0];
+    use_device(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool other = s != h->stream;
+    cudaEvent_t e = nullptr;
+    if (other) {  // the launch stream waits for `stream`, and `stream` for the results
+        HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        HCUDA(cudaEventRecord(e, s));
+        HCUDA(cudaStreamWaitEvent(h->stream, e, 0));
+    }
+    homln_status st = homln_batch_analyse(nets, count, masks.data(), 1);
+    if (other) {
+        HCUDA(cudaEventRecord(e, h->stream));
+        HCUDA(cudaStreamWaitEvent(s, e, 0));
+        cudaEventDestroy(e);
+    }
+    if (st != HOMLN_OK) fail(st, homln_last_error());
+    API_END
+}
+
 }  // extern "C"
 
 // A captured analysis: the plan's buffers, the graphs it writes, and the instantiated graph.

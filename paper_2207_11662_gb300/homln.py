@@ -35,7 +35,7 @@ EXPORTS = [
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
     "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness", "homln_export_partials",
     "homln_import_partials", "homln_graph_capture", "homln_graph_launch", "homln_graph_destroy",
-    "homln_shard_partials",
+    "homln_shard_partials", "homln_batch_closeness",
 ]
 
 
@@ -121,6 +121,7 @@ def _load():
         "homln_graph_capture": (S, [POINTER(c_void_p), c_int32, POINTER(c_uint64), c_int32, POINTER(c_void_p)]),
         "homln_graph_launch": (S, [c_void_p]),
         "homln_shard_partials": (S, [c_void_p, c_int32, c_uint64, c_int32, c_int32, c_void_p, c_void_p]),
+        "homln_batch_closeness": (S, [POINTER(c_void_p), c_int32, c_void_p]),
         "homln_graph_destroy": (S, [c_void_p]),
         "homln_import_partials": (S, [c_void_p, c_int32, c_uint64, c_void_p, c_void_p]),
         "homln_last_error": (c_char_p, []),
@@ -269,6 +270,12 @@ def homln_graph_capture(handles, masks, with_and: bool = True) -> int:
 def homln_shard_partials(h, which: int, layer_mask: int, rank: int, world: int, farness, reach) -> None:
     _check(lib.homln_shard_partials(h, int(which), int(layer_mask), int(rank), int(world), ptr(farness), ptr(reach)),
            "homln_shard_partials")
+
+
+def homln_batch_closeness(handles, stream=None) -> None:
+    n = len(handles)
+    hs = (c_void_p * n)(*handles)
+    _check(lib.homln_batch_closeness(hs, n, c_void_p(stream) if stream else None), "homln_batch_closeness")
 
 
 def homln_graph_launch(g) -> None:

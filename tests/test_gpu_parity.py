@@ -684,3 +684,21 @@ def test_sharded_partials_sum_to_the_analysis(H, world):
     assert b.topk(-1, 7, sel).cpu().numpy().tolist() == ref.topk(-1, 7, osel).tolist()
     a.close()
     b.close()
+
+
+def test_batch_closeness_on_an_explicit_stream(H):
+    """homln_batch_closeness: every layer and the all-layer AND graph of each handle, ordered
+    with the given stream."""
+    import torch
+    nets = synth.homln_batch(count=4, seed=131, n_range=(300, 1500), layer_range=(2, 4))
+    gs = [H.Network(net.n, to_dev(net.layers)) for net in nets]
+    side = torch.cuda.Stream()
+    H.homln_batch_closeness([g.h for g in gs], side.cuda_stream)
+    side.synchronize()
+    for g, net in zip(gs, nets):
+        ref = O.OracleHoMLN(net.n, net.layers)
+        full = (1 << net.n_layers) - 1
+        for i in range(net.n_layers):
+            check_graph(*g.layer_closeness(i), ref.layer(i))
+        check_graph(*g.and_closeness(full), ref.and_graph(full))
+        g.close()
