@@ -507,7 +507,7 @@ def paper_like(args, dev):
     out["min_psi_ms"] = round(psi_min, 3)
     out["max_theta_ms"] = {k: round(v, 3) for k, v in theta_max.items()}
     out["max_theta_over_min_psi"] = {k: round(v / psi_min, 3) for k, v in theta_max.items()}
-    out["note"] = ("accuracy in percent (Jaccard is the paper's 'accuracy'); paper (Table 2) S-1/S-2/S-3 mean "
+    out["note"] = ("accuracy in percent (Jaccard is what the paper calls accuracy); paper (Table 2) S-1/S-2/S-3 mean "
                    "Jaccard CC1 43.56/55.95/48.87, CC2 46.77/55.20/50.90 on PaRMAT data, context only")
     return out
 

@@ -65,7 +65,7 @@ typedef enum homln_status {
     HOMLN_ECUDA = 3,    /* a CUDA runtime call failed (message in homln_last_error) */
     HOMLN_ERANGE = 4,   /* an output capacity is too small, or a value left its exact range */
     HOMLN_ETIMEOUT = 5, /* a bounded device-side wait gave up (the kernel returned early) */
-    HOMLN_EBUSY = 6     /* the handle is in use by a batched launch */
+    HOMLN_EBUSY = 6     /* the handle or its results are in use by a captured graph */
 } homln_status;
 
 /* homln_create flags */
@@ -83,13 +83,13 @@ typedef enum homln_heuristic { HOMLN_NAIVE = 0, HOMLN_CC1 = 1, HOMLN_CC2 = 2 } h
 /* CC-node selection rule.
  *   TOPK_PERCENT: the k = ceil(percent * n / 100) highest scores (double arithmetic).
  *   TOPK_COUNT:   the k highest scores (k clamped to [0, n]).
- *   GE_MEAN:      every node whose score is >= the mean score ("same or above
- *                 average", Section 4), decided exactly on the float64 scores.
+ *   GE_MEAN:      every node whose score is at least the mean score (Section 4),
+ *                 decided exactly on the float64 scores.
  *   GT_MEAN:      strictly above the mean.
  * Ranking: score descending, equal scores by ascending node id.
- * cc1_overlap is CC1's "significant overlap" threshold theta (Section 5.1 leaves
- * it undefined): a common CC node u is kept iff |AND of C_i(u)| >= theta*|OR of C_i(u)|
- * and the union is non-empty. */
+ * cc1_overlap is the threshold theta of CC1's overlap test (Section 5.1 asks for a large
+ * overlap of central neighbours without defining it): a common CC node u is kept iff
+ * |AND of C_i(u)| >= theta*|OR of C_i(u)| and the union is non-empty. */
 typedef enum homln_select_mode {
     HOMLN_TOPK_PERCENT = 0,
     HOMLN_TOPK_COUNT = 1,
@@ -117,7 +117,7 @@ typedef struct homln_allocator {
 } homln_allocator;
 
 /* Accuracy of an estimated CC-node set against ground truth (Section 5,
- * Section 6.1): the paper's "accuracy" is the Jaccard coefficient.
+ * Section 6.1): what the paper calls accuracy is the Jaccard coefficient.
  *   jaccard = tp/(tp+fp+fn) (1 when all three are 0), precision = tp/(tp+fp),
  *   recall = tp/(tp+fn), f1 = 2tp/(2tp+fp+fn) (each 0 when its denominator is 0). */
 typedef struct homln_accuracy_t {

@@ -27,9 +27,9 @@ depend on an average (at or above the average) are taken exactly on those
 float64 values with ``fractions.Fraction`` (no summation-order dependence).
 
 Parity status: everything is pinned by tests in ``tests/test_oracle_*.py``
-except the CC1 overlap threshold, which the paper leaves undefined ("significant
-overlap", Section 5.1): parity unpinned for the value of theta (the steps around
-it are pinned by a hand-worked example).
+except the CC1 overlap threshold, which the paper leaves undefined (Section 5.1 asks
+for a large overlap without a number): parity unpinned for the value of theta (the
+steps around it are pinned by a hand-worked example).
 """
 from __future__ import annotations
 
