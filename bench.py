@@ -212,8 +212,10 @@ def measured_traffic(workload: str, tiles: int):
 
 
 def bfs_bytes(prof: dict) -> float:
-    """Algorithmic bytes of the BFS launches (the byte model is stated in the design doc): the bytes
-    the kernel's loads and stores request, counted by its instrumented variant."""
+    """Algorithmic bytes of the BFS launches: the bytes the kernel's loads and stores request,
+    counted by its instrumented variant -- per gathered frontier word 8 B, per scanned or pushed
+    column index 4 B, per atomic OR 8 B, and per visited vertex its seen/next words, row bounds,
+    F/R and per-vertex bytes (a load shared by the lanes of one vertex counted once)."""
     return float(prof["bytes"])
 
 

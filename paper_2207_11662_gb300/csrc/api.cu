@@ -63,7 +63,7 @@ static cudaMemPool_t device_pool() {
         uint64_t keep = kPoolKeepBytes;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         // Memory freed on one stream is reused on another only through an event dependency the
-        // program made itself: with many handles and side streams, the driver's own cross-stream
+        // program made itself: with many handles and side streams, the CUDA driver's own cross-stream
         // reuse (completion checks, inserted dependencies) made allocations very slow.
         int off = 0;
         cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowOpportunistic, &off);
