@@ -94,6 +94,7 @@ struct Tile {
     uint8_t *quiet;
     uint8_t *fresh;
     uint8_t *pushed;  // a top-down level ORed words into the vertex's next frontier words
+    int32_t *err;     // device error word (debug builds report bad neighbour ids in it)
     uint64_t *F;
     uint32_t *R;
     unsigned long long *ctr;
@@ -267,6 +268,19 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b) {
 #endif
 constexpr int kUnroll = HOMLN_GATHER_UNROLL;
 
+#ifndef HOMLN_DEBUG
+#define HOMLN_DEBUG 0
+#endif
+// Debug builds (-DHOMLN_DEBUG=1) check every neighbour id before it is used: an id outside
+// [0, n) records DEV_BAD_ID in the error word and the neighbour is treated as absent. Release
+// builds compile the check away.
+__device__ __forceinline__ bool id_ok(const Tile &a, int64_t u) {
+    if (!HOMLN_DEBUG) return true;
+    if (u >= 0 && u < a.n) return true;
+    dev_fail(a.err, DEV_BAD_ID);
+    return false;
+}
+
 // OR the frontier words (this lane's K of them) of neighbours rb+p, rb+p+S, ... into acc;
 // stop once every bit this lane still needs is present. kUnroll neighbours are gathered per
 // step (past the row end the loads are predicated off), and the column indices of the next
@@ -286,7 +300,7 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
         uint64_t f[U][K];
 #pragma unroll
         for (int i = 0; i < U; ++i) {
-            if (u[i] >= 0) {
+            if (u[i] >= 0 && id_ok(a, u[i])) {
                 ldw<K>(cur + (int64_t)u[i] * W + q * K, f[i]);
             } else {
 #pragma unroll
@@ -327,8 +341,9 @@ __device__ __forceinline__ int64_t gather_or_warp(const Tile &a, const uint64_t 
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const int64_t jj = j + (int64_t)i * S;
-            if (jj < re) {
-                ldw<K>(cur + (int64_t)__ldg(a.pcol + jj) * W + q * K, f[i]);
+            const int32_t uj = jj < re ? __ldg(a.pcol + jj) : -1;
+            if (jj < re && id_ok(a, uj)) {
+                ldw<K>(cur + (int64_t)uj * W + q * K, f[i]);
                 ++it;
             } else {
 #pragma unroll
@@ -478,6 +493,7 @@ __device__ void phase_start_push(const Tile &a, uint64_t *fa, int32_t s0, int32_
             if (a.rowptr[s0 + mid] <= e) lo = mid; else hi = mid;
         }
         const int32_t u = __ldg(a.col + e);
+        if (!id_ok(a, u)) continue;
         atomicOr(reinterpret_cast<unsigned long long *>(fa + (int64_t)u * W + (lo >> 6)), 1ull << (lo & 63));
         a.pushed[u] = 1;
         if (STATS) { st[ST_BYTES] += 4 + 8 + 1; st[ST_PUSHED] += 1; st[ST_PUSHWORDS] += 1; }
@@ -703,7 +719,7 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint
         for (int64_t j = rb + p; j < re; j += S) {
             const int64_t u = __ldg(a.col + j);
             if (STATS && q == 0) { st[ST_PUSHED] += 1; st[ST_BYTES] += 5; }
-            if (a.quiet[u] >= QUIET) continue;
+            if (!id_ok(a, u) || a.quiet[u] >= QUIET) continue;
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (f[k]) {
@@ -833,6 +849,7 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
         a.quiet = quiet;
         a.fresh = fresh;
         a.pushed = pushed;
+        a.err = A.err;
         a.F = g.F;
         a.R = g.R;
         a.ctr = ctr;
@@ -893,6 +910,7 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     a.quiet = A.quiet;
     a.fresh = A.fresh;
     a.pushed = A.pushed;
+    a.err = A.err;
     a.F = g.F;
     a.R = g.R;
     a.ctr = A.ctr;
