@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -342,7 +343,8 @@ using Items = std::vector<std::pair<homln_t, GraphState *>>;
 
 // Make every graph of `todo` ready for a BFS launch on h's stream: result buffers allocated
 // (kept if they exist), BFS graphs built, other handles' streams ordered before h's.
-std::vector<BfsJob> prepare_items(homln_t h, const Items &todo) {
+// `overlap`, if given, enqueues work of its own on h's stream while the lanes relabel.
+std::vector<BfsJob> prepare_items(homln_t h, const Items &todo, const std::function<void()> &overlap = {}) {
     std::vector<BfsJob> jobs;
     std::vector<homln_t> others;
     std::vector<std::pair<homln_t, GraphState *>> prep;  // graphs whose BFS form must be (re)built
@@ -392,6 +394,7 @@ std::vector<BfsJob> prepare_items(homln_t h, const Items &todo) {
         }
         g->bfs_ready = true;
     }
+    if (overlap) overlap();
     lanes_join(h, nl);
     for (homln_t o : others) {  // h's stream waits for the CSRs and outputs queued on the other streams
         cudaEvent_t e;
@@ -721,8 +724,23 @@ homln_status homln_analyse(homln_t h, uint64_t layer_mask, int32_t with_and) {
     if (!h) fail(HOMLN_EINVAL, "null handle");
     use_device(h);
     std::vector<GraphState *> gs;
-    for (int i : mask_layers(h, layer_mask)) gs.push_back(h->layers[i].get());
-    if (with_and) gs.push_back(&and_graph(h, layer_mask));
+    Items layers;
+    for (int i : mask_layers(h, layer_mask)) {
+        gs.push_back(h->layers[i].get());
+        if (!h->layers[i]->analysed) layers.push_back({h, h->layers[i].get()});
+    }
+    // the AND graph is built, and relabelled, on the handle's stream while the lanes relabel the layers
+    GraphState *andg = nullptr;
+    prepare_items(h, layers, [&] {
+        if (!with_and) return;
+        andg = &and_graph(h, layer_mask);
+        if (!andg->analysed && !andg->bfs_ready) {  // a rebuild (relabelling changed) is left to analyse_many
+            bfs_prepare(andg->csr, h->directed ? &andg->csr_in : nullptr, h->tuning.relabel != 0, andg->bfs,
+                        &h->al, h->stream);
+            andg->bfs_ready = true;
+        }
+    });
+    if (andg) gs.push_back(andg);
     analyse_many(h, gs);
     API_END
 }

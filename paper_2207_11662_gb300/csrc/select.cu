@@ -436,6 +436,65 @@ __global__ void k_accuracy_ratios(const unsigned long long *c3, double *out4) {
     out4[3] = c3[0] > 0 ? __ddiv_rn(2.0 * tp, 2.0 * tp + fp + fn) : 0.0;
 }
 
+// Both id lists into their bitmaps in one pass (thread i takes pred[i] and truth[i]).
+__global__ void k_lists_bits(const int32_t *__restrict__ pred, int32_t n_pred, const int32_t *__restrict__ truth,
+                             int32_t n_truth, int32_t n, uint32_t *__restrict__ P, uint32_t *__restrict__ T, int32_t *err) {
+    const int32_t m = n_pred > n_truth ? n_pred : n_truth;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (i < n_pred) {
+            const int32_t v = pred[i];
+            if (v < 0 || v >= n) dev_fail(err, DEV_BAD_ID);
+            else atomicOr(&P[v >> 5], 1u << (v & 31));
+        }
+        if (i < n_truth) {
+            const int32_t v = truth[i];
+            if (v < 0 || v >= n) dev_fail(err, DEV_BAD_ID);
+            else atomicOr(&T[v >> 5], 1u << (v & 31));
+        }
+    }
+}
+
+// Confusion counts of the two bitmaps; the last block to finish turns them into the ratios.
+// out: tp, fp, fn (uint64), then jaccard, precision, recall, f1 (double), then a block counter.
+struct AccOut {
+    unsigned long long c3[3];
+    double r4[4];
+    unsigned int done;
+};
+
+__global__ void k_confusion_ratios(int32_t nw, const uint32_t *__restrict__ P, const uint32_t *__restrict__ T,
+                                   AccOut *out) {
+    unsigned long long tp = 0, fp = 0, fn = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
+        const uint32_t p = P[i], t = T[i];
+        tp += __popc(p & t);
+        fp += __popc(p & ~t);
+        fn += __popc(~p & t);
+    }
+    tp = warp_sum(tp);
+    fp = warp_sum(fp);
+    fn = warp_sum(fn);
+    if ((threadIdx.x & 31) == 0) {
+        if (tp) atomicAdd(out->c3 + 0, tp);
+        if (fp) atomicAdd(out->c3 + 1, fp);
+        if (fn) atomicAdd(out->c3 + 2, fn);
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(&out->done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const unsigned long long c0 = atomicAdd(out->c3 + 0, 0ull), c1 = atomicAdd(out->c3 + 1, 0ull),
+                             c2 = atomicAdd(out->c3 + 2, 0ull);
+    const double dtp = (double)c0, dfp = (double)c1, dfn = (double)c2;
+    out->r4[0] = (c0 + c1 + c2) > 0 ? __ddiv_rn(dtp, dtp + dfp + dfn) : 1.0;
+    out->r4[1] = (c0 + c1) > 0 ? __ddiv_rn(dtp, dtp + dfp) : 0.0;
+    out->r4[2] = (c0 + c2) > 0 ? __ddiv_rn(dtp, dtp + dfn) : 0.0;
+    out->r4[3] = c0 > 0 ? __ddiv_rn(2.0 * dtp, 2.0 * dtp + dfp + dfn) : 0.0;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -554,32 +613,30 @@ void bits_and(int32_t nwords, uint32_t *d_acc, const uint32_t *d_other, cudaStre
 
 void accuracy_counts(int32_t n, const int32_t *d_pred, int32_t n_pred, const int32_t *d_truth, int32_t n_truth,
                      homln_accuracy_t *h_out, int32_t *d_err, Alloc *al, cudaStream_t s) {
+    // one scratch block: the two bitmaps, then the counts, ratios and block counter (the even
+    // word count 2 * nw keeps AccOut 8-byte aligned)
     const int32_t nw = (int32_t)ceil_div(n, 32);
-    DBuf<uint32_t> P, T;
-    DBuf<unsigned long long> c3;
-    DBuf<double> r4;
-    if (!P.alloc(al, nw) || !T.alloc(al, nw) || !c3.alloc(al, 3) || !r4.alloc(al, 4))
-        fail(HOMLN_ENOMEM, "accuracy scratch");
-    HCUDA(cudaMemsetAsync(P.p, 0, sizeof(uint32_t) * nw, s));
-    HCUDA(cudaMemsetAsync(T.p, 0, sizeof(uint32_t) * nw, s));
-    HCUDA(cudaMemsetAsync(c3.p, 0, sizeof(unsigned long long) * 3, s));
-    if (n_pred > 0) launch(k_list_bits, grid_for(n_pred), 256, 0, s, d_pred, n_pred, n, P.p, d_err);
-    if (n_truth > 0) launch(k_list_bits, grid_for(n_truth), 256, 0, s, d_truth, n_truth, n, T.p, d_err);
-    launch(k_confusion, grid_for(nw), 256, 0, s, nw, P.p, T.p, c3.p);
-    launch(k_accuracy_ratios, 1, 32, 0, s, c3.p, r4.p);
+    static_assert(sizeof(AccOut) % 4 == 0, "AccOut is a whole number of words");
+    const size_t words = 2 * (size_t)nw + sizeof(AccOut) / 4;
+    DBuf<uint32_t> scratch;
+    if (!scratch.alloc(al, words)) fail(HOMLN_ENOMEM, "accuracy scratch");
+    uint32_t *P = scratch.p, *T = scratch.p + nw;
+    AccOut *out = reinterpret_cast<AccOut *>(scratch.p + 2 * (size_t)nw);
+    HCUDA(cudaMemsetAsync(scratch.p, 0, sizeof(uint32_t) * words, s));
+    const int32_t m = n_pred > n_truth ? n_pred : n_truth;
+    if (m > 0) launch(k_lists_bits, grid_for(m), 256, 0, s, d_pred, n_pred, d_truth, n_truth, n, P, T, d_err);
+    launch(k_confusion_ratios, grid_for(nw), 256, 0, s, nw, (const uint32_t *)P, (const uint32_t *)T, out);
     HCUDA(cudaGetLastError());
-    unsigned long long h[3];
-    double r[4];
-    HCUDA(cudaMemcpyAsync(h, c3.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-    HCUDA(cudaMemcpyAsync(r, r4.p, sizeof(r), cudaMemcpyDeviceToHost, s));
+    AccOut h;
+    HCUDA(cudaMemcpyAsync(&h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
     HCUDA(cudaStreamSynchronize(s));
-    h_out->tp = (int64_t)h[0];
-    h_out->fp = (int64_t)h[1];
-    h_out->fn = (int64_t)h[2];
-    h_out->jaccard = r[0];
-    h_out->precision = r[1];
-    h_out->recall = r[2];
-    h_out->f1 = r[3];
+    h_out->tp = (int64_t)h.c3[0];
+    h_out->fp = (int64_t)h.c3[1];
+    h_out->fn = (int64_t)h.c3[2];
+    h_out->jaccard = h.r4[0];
+    h_out->precision = h.r4[1];
+    h_out->recall = h.r4[2];
+    h_out->f1 = h.r4[3];
 }
 
 // The accuracy kernels run on scratch the caller provides (no allocation here).

@@ -349,6 +349,31 @@ def test_host_buffers_match_device_buffers(H):
     H.homln_destroy(h)
 
 
+def test_accuracy_edge_cases_match_the_oracle(H):
+    """Accuracy of id lists against the oracle, exactly: empty lists on either or both sides,
+    repeated ids, a node count that is not a multiple of 32, and lists long enough that the
+    counts come from many blocks (the last of which forms the ratios)."""
+    rng = np.random.default_rng(5)
+    for n in (2, 33, 1000, 2_000_003):
+        h = H.homln_create(n, [(np.array([0], np.int32), np.array([1], np.int32))])
+        try:
+            k = min(n, 5000 if n < 10**6 else 400_000)
+            cases = [(np.zeros(0, np.int32), np.zeros(0, np.int32)),
+                     (rng.choice(n, k, replace=False), np.zeros(0, np.int32)),
+                     (np.zeros(0, np.int32), rng.choice(n, k, replace=False)),
+                     (rng.choice(n, k, replace=True), rng.choice(n, k, replace=True)),
+                     (rng.choice(n, k, replace=False), rng.choice(n, max(1, k // 3), replace=False)),
+                     (np.full(7, n - 1), np.array([n - 1]))]
+            for pred, truth in cases:
+                pred = pred.astype(np.int32)
+                truth = truth.astype(np.int32)
+                got = H.homln_accuracy(h, pred, pred.size, truth, truth.size)
+                want = O.accuracy(pred, truth)
+                assert got == want, (n, pred.size, truth.size)
+        finally:
+            H.homln_destroy(h)
+
+
 def test_error_statuses(H):
     n = 50
     bad = (np.array([0, 50], np.int32), np.array([1, 2], np.int32))
