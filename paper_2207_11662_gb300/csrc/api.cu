@@ -250,6 +250,29 @@ void lanes_join(homln_t h, int count) {
     }
 }
 
+// Lanes forked for `count` work items, joined into the handle's stream by join() or, when an
+// error unwinds the call first, by the destructor (which then ignores CUDA errors): the
+// handle's stream never runs ahead of lane work that was already queued.
+struct LaneScope {
+    homln_t h;
+    int count;
+    LaneScope(homln_t h_, int c) : h(h_), count(c) { lanes_fork(h, count); }
+    LaneScope(const LaneScope &) = delete;
+    LaneScope &operator=(const LaneScope &) = delete;
+    void join() {
+        const int c = count;
+        count = 0;
+        lanes_join(h, c);
+    }
+    ~LaneScope() {
+        if (count <= 0) return;
+        for (int i = 0; i < Lanes::kCount; ++i)
+            if (cudaEventRecord(h->lanes.done[i], h->lanes.s[i]) == cudaSuccess)
+                cudaStreamWaitEvent(h->stream, h->lanes.done[i], 0);
+        cudaGetLastError();
+    }
+};
+
 // The CSR whose rows are the neighbours that reach a vertex: the in-edges of a directed graph.
 const Csr &in_csr(homln_t h, const GraphState &g) { return h->directed ? g.csr_in : g.csr; }
 
@@ -380,7 +403,7 @@ std::vector<BfsJob> prepare_items(homln_t h, const Items &todo, const std::funct
     // the relabellings of h's graphs run on h's lanes side by side; other handles' on their streams
     int nl = 0;
     for (const auto &it : prep) nl += it.first == h;
-    lanes_fork(h, nl);
+    LaneScope lanes(h, nl);
     int k = 0;
     for (const auto &it : prep) {
         homln_t o = it.first;
@@ -395,7 +418,7 @@ std::vector<BfsJob> prepare_items(homln_t h, const Items &todo, const std::funct
         g->bfs_ready = true;
     }
     if (overlap) overlap();
-    lanes_join(h, nl);
+    lanes.join();
     for (homln_t o : others) {  // h's stream waits for the CSRs and outputs queued on the other streams
         cudaEvent_t e;
         HCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -549,13 +572,13 @@ void selections_of(homln_t h, const std::vector<GraphState *> &gs, const homln_s
         g->selections.emplace(key, std::move(s));
     }
     if (todo.empty()) return;
-    lanes_fork(h, (int)todo.size());
+    LaneScope lanes(h, (int)todo.size());
     for (size_t i = 0; i < todo.size(); ++i) {
         const int j = (int)(i % Lanes::kCount);
         todo[i].second->count = select_nodes(h->n, todo[i].first->cc.p, sel, todo[i].second->ranked.p,
                                              todo[i].second->bits.p, h->err.p, &h->lanes.al[j], h->lanes.s[j]);
     }
-    lanes_join(h, (int)todo.size());
+    lanes.join();
 }
 
 GraphState &or_graph(homln_t h, uint64_t mask) {
@@ -644,7 +667,7 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
         }
         h->layers.push_back(std::make_unique<GraphState>());
     }
-    lanes_fork(h.get(), n_layers);
+    LaneScope lanes(h.get(), n_layers);
     for (int i = 0; i < n_layers; ++i) {
         const int j = i % Lanes::kCount;
         GraphState &g = *h->layers[i];
@@ -652,7 +675,7 @@ homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge
         if (h->directed)
             build_csr(n_nodes, pd[i], ps[i], edge_counts[i], g.csr_in, h->err.p, &h->lanes.al[j], h->lanes.s[j], true);
     }
-    lanes_join(h.get(), n_layers);
+    lanes.join();
     check_device_error(h.get());
     *out = h.release();
     API_END
