@@ -243,8 +243,13 @@ void or_union(int32_t n, const std::vector<const Csr *> &layers, Csr &out, Alloc
 // Edge list ascending (u, v) of a CSR: pairs u < v (nnz/2 of them) of an undirected graph, or
 // every entry of a directed one.
 void csr_edge_list(const Csr &g, int32_t *d_src, int32_t *d_dst, Alloc *al, cudaStream_t s, bool directed = false);
-// Degree-descending relabelling: perm[new] = old, inv[old] = new; builds the relabelled CSR.
-void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv, Alloc *al, cudaStream_t s);
+// Relabelling for the BFS: degree descending (degrees of g), then id ascending, except that
+// the vertices of small connected components (at most 8 vertices; weakly connected through g
+// and `other` when g is one direction of a directed graph) come last. perm[new] = old,
+// inv[old] = new; builds the relabelled CSR, and split[0] (on the device) = the number of
+// vertices before the small components: vertices 0 .. split[0]-1 form whole components.
+void relabel_by_degree(const Csr &g, const Csr *other, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv,
+                       DBuf<int32_t> &split, Alloc *al, cudaStream_t s);
 // The same relabelling applied to another CSR over the same vertices.
 void relabel_apply(const Csr &g, const int32_t *perm, const int32_t *inv, Csr &out, Alloc *al, cudaStream_t s);
 
@@ -280,12 +285,15 @@ struct BfsStats {  // filled by an instrumented run
     int teams = 0;             // teams of the last launch
 };
 
-// The graph the BFS traverses: the CSR itself, or its degree-descending relabelling (perm[new] = old).
+// The graph the BFS traverses: the CSR itself, or its relabelling (perm[new] = old), in which
+// vertices 0 .. split[0]-1 form whole (weakly) connected components and the small components
+// follow.
 // A directed graph also carries its in-edge CSR (csr_in), which the bottom-up levels read.
 struct BfsGraph {
     Csr csr;
     Csr csr_in;
     DBuf<int32_t> perm;
+    DBuf<int32_t> split;  // relabelled graphs: [0] = vertices before the small components
     bool relabeled = false;
     bool directed = false;
 };

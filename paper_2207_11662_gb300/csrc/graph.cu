@@ -184,11 +184,75 @@ __global__ void k_write_pairs(int32_t n, const int32_t *__restrict__ col, const 
     }
 }
 
-__global__ void k_degree_keys(int32_t n, const int64_t *__restrict__ rp, uint64_t *__restrict__ keys) {
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint64_t deg = (uint64_t)(rp[v + 1] - rp[v]);
-        keys[v] = ((NODE_MASK - deg) << NODE_BITS) | (uint64_t)v;  // degree descending, then id ascending
+// Sort keys for the BFS order: vertices of small components (at most kSmallComponent vertices)
+// last, otherwise degree descending, then id ascending. A thread explores v's component
+// breadth-first, along the rows of `a` and (directed: weak components) of `b`, and stops as
+// soon as it holds more than kSmallComponent vertices or meets a row that long. The blocks add
+// up their small-component vertices; the last block to finish writes split[0] = n - their
+// count, the number of vertices placed before them.
+constexpr int kSmallComponent = 8;
+
+__device__ __forceinline__ bool small_component(int32_t v, int32_t n, const int64_t *__restrict__ ra,
+                                                const int32_t *__restrict__ ca, const int64_t *__restrict__ rb,
+                                                const int32_t *__restrict__ cb) {
+    constexpr int S = kSmallComponent;
+    int32_t vis[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) vis[k] = -1;
+    vis[0] = v;
+    int cnt = 1;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        if (i >= cnt) break;
+        int32_t x = -1;
+#pragma unroll
+        for (int k = 0; k < S; ++k)
+            if (k == i) x = vis[k];
+        for (int side = 0; side < (rb ? 2 : 1); ++side) {
+            const int64_t *rp = side ? rb : ra;
+            const int32_t *col = side ? cb : ca;
+            const int64_t e0 = rp[x], e1 = rp[x + 1];
+            if (e1 - e0 >= S) return false;
+            for (int64_t j = e0; j < e1; ++j) {
+                const int32_t u = col[j];
+                if (u < 0 || u >= n) continue;
+                bool seen = false;
+#pragma unroll
+                for (int k = 0; k < S; ++k) seen |= vis[k] == u;
+                if (seen) continue;
+                if (cnt == S) return false;
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+                    if (k == cnt) vis[k] = u;
+                ++cnt;
+            }
+        }
     }
+    return true;
+}
+
+__global__ void k_degree_keys(int32_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const int64_t *__restrict__ rp2, const int32_t *__restrict__ col2,
+                              unsigned int *__restrict__ ctr, int32_t *__restrict__ split,
+                              uint64_t *__restrict__ keys) {
+    __shared__ unsigned int block_small;
+    if (threadIdx.x == 0) block_small = 0;
+    __syncthreads();
+    unsigned int mine = 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t deg = (uint64_t)(rp[v + 1] - rp[v]);
+        const uint64_t small = small_component(v, n, rp, col, rp2, col2) ? 1 : 0;
+        mine += (unsigned int)small;
+        keys[v] = (small << (2 * NODE_BITS)) | ((NODE_MASK - deg) << NODE_BITS) | (uint64_t)v;
+    }
+    if (mine) atomicAdd(&block_small, mine);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (block_small) atomicAdd(ctr, block_small);
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    *split = n - (int32_t)atomicAdd(ctr, 0u);
 }
 
 __global__ void k_perm_from_keys(int32_t n, const uint64_t *__restrict__ keys, int32_t *__restrict__ perm,
@@ -349,14 +413,19 @@ void relabel_apply(const Csr &g, const int32_t *perm, const int32_t *inv, Csr &o
     HCUDA(cudaGetLastError());
 }
 
-void relabel_by_degree(const Csr &g, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv, Alloc *al, cudaStream_t s) {
+void relabel_by_degree(const Csr &g, const Csr *other, Csr &out, DBuf<int32_t> &perm, DBuf<int32_t> &inv,
+                       DBuf<int32_t> &split, Alloc *al, cudaStream_t s) {
     const int32_t n = g.n;
     DBuf<uint64_t> vkeys;
-    if (!vkeys.alloc(al, n) || !inv.alloc(al, n) || !perm.alloc(al, n)) fail(HOMLN_ENOMEM, "relabel scratch");
-    launch(k_degree_keys, grid_for(n), 256, 0, s, n, g.rowptr.p, vkeys.p);
-    // the keys are generated in id order, so a stable sort on the degree bits alone leaves equal
-    // degrees in ascending id order
-    radix_sort_u64(vkeys.p, nullptr, n, NODE_BITS, 2 * NODE_BITS, al, s);
+    DBuf<unsigned int> ctr;
+    if (!vkeys.alloc(al, n) || !inv.alloc(al, n) || !perm.alloc(al, n) || !split.alloc(al, 1) || !ctr.alloc(al, 2))
+        fail(HOMLN_ENOMEM, "relabel scratch");
+    HCUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned int), s));
+    launch(k_degree_keys, grid_for(n), 256, 0, s, n, g.rowptr.p, g.col.p, other ? other->rowptr.p : nullptr,
+           other ? other->col.p : nullptr, ctr.p, split.p, vkeys.p);
+    // the keys are generated in id order, so a stable sort on the small-component bit and the
+    // degree bits leaves equal keys in ascending id order
+    radix_sort_u64(vkeys.p, nullptr, n, NODE_BITS, 2 * NODE_BITS + 1, al, s);
     launch(k_perm_from_keys, grid_for(n), 256, 0, s, n, vkeys.p, perm.p, inv.p);
     relabel_apply(g, perm.p, inv.p, out, al, s);
 }

@@ -46,6 +46,8 @@ struct GraphDesc {
     int32_t b0;             // first source batch (a shard's rank; 0 unsharded)
     int32_t bstride;        // batch stride (a shard's world size; 1 unsharded)
     int32_t pad;
+    const int32_t *split;   // relabelled graphs: [0] = G, vertices 0 .. G-1 form whole components, so
+                            // no other vertex is connected to them (nullptr: G = n, no split)
 };
 
 struct TeamArgs {
@@ -74,7 +76,7 @@ struct TeamArgs {
     int32_t phantom;            // tests: blocks every team barrier waits for in vain
 };
 
-// First vertex of a degree-descending graph whose degree is below thr (binary search).
+// First vertex of a degree-descending vertex range 0 .. n-1 whose degree is below thr (binary search).
 __device__ __forceinline__ int32_t first_below(const int64_t *__restrict__ rp, int32_t n, int64_t thr) {
     int32_t lo = 0, hi = n;
     while (lo < hi) {
@@ -99,6 +101,7 @@ struct Tile {
     uint32_t *R;
     unsigned long long *ctr;
     int32_t n;
+    int32_t gend;   // vertices 0 .. gend-1 form whole components, disconnected from the rest
     int32_t hub_block_end;
     int32_t hub_warp_end;
     int32_t rank;   // block index within the team
@@ -449,21 +452,30 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
 
 // ---------------------------------------------------------------- phases
 
-// Level 0 of a batch: seen = own source bit (plus padding bits for a short last batch), both
-// frontier buffers 0, the per-vertex bytes 0.
+// Level 0 of a batch: seen = the bits of the sources that cannot reach the vertex (the padding
+// bits of a short last batch; the batch's sources on the other side of the split at gend) and
+// its own source bit; both frontier buffers 0; the per-vertex bytes 0, except that a vertex that
+// no other source of the batch can reach (none on its side of the split, or no in-edges) is
+// quiet from the start. The unreachable bits never arrive, so without them in `seen` no vertex
+// of a batch that mixes the two sides would ever become full.
 template <int W, bool STATS>
 __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int32_t s0, int32_t ns,
                                   unsigned long long *st) {
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
+    // the batch's sources below the split are bits 0 .. split-1, the rest split .. ns-1
+    const int32_t split = min(max(a.gend - s0, 0), ns);
     for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
         const int64_t v = i / W;
         const int wi = (int)(i % W);
         const int lo = wi * 64;
-        uint64_t x = 0;
-        if (lo >= ns) x = ~0ull;
-        else if (lo + 64 > ns) x = ~0ull << (ns - lo);
-        if (v >= s0 && v < (int64_t)s0 + ns) {
+        // bits c0 .. c1-1 of the batch can reach v; the rest are set
+        const int32_t c0 = v < a.gend ? 0 : split, c1 = v < a.gend ? split : ns;
+        const int32_t b0 = max(c0 - lo, 0), b1 = min(c1 - lo, 64);
+        uint64_t x = ~0ull;
+        if (b1 > b0) x = ~((b1 - b0 == 64 ? ~0ull : ((1ull << (b1 - b0)) - 1)) << b0);
+        const bool source = v >= s0 && v < (int64_t)s0 + ns;
+        if (source) {
             const int b = (int)(v - s0);
             if ((b >> 6) == wi) x |= 1ull << (b & 63);
         }
@@ -471,11 +483,12 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int
         fa[i] = 0;
         fb[i] = 0;
         if (wi == 0) {
-            a.quiet[v] = 0;
+            const bool lonely = c1 - c0 - (source ? 1 : 0) <= 0 || a.prow[v + 1] == a.prow[v];
+            a.quiet[v] = lonely ? QUIET : 0;
             a.fresh[v] = 0;
             a.pushed[v] = 0;
         }
-        if (STATS) st[ST_BYTES] += 24 + 3 * (wi == 0);
+        if (STATS) st[ST_BYTES] += 24 + (wi == 0 ? 3 + 16 : 0);
     }
 }
 
@@ -857,10 +870,11 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
         // hub tiers: rows of at least HOMLN_BLOCK_TIER_ITERS (4) iterations per slot of a block go
         // to a whole block, the rest with at least HOMLN_WARP_TIER_ITERS (8) per slot of a warp to
         // a whole warp (measured on GB300: warp threshold 8 beat 2, 4, 12, 16 and 32)
+        a.gend = g.split ? min(max(*g.split, 0), g.n) : g.n;
         a.hub_block_end =
-            g.by_degree ? first_below(g.prow, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+            g.by_degree ? first_below(g.prow, a.gend, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
         a.hub_warp_end = g.by_degree
-                             ? max(a.hub_block_end, first_below(g.prow, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                             ? max(a.hub_block_end, first_below(g.prow, a.gend, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
                              : 0;
         a.rank = rank;
         a.tsize = tsize;
@@ -915,10 +929,11 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     a.R = g.R;
     a.ctr = A.ctr;
     a.n = g.n;
+    a.gend = g.split ? min(max(*g.split, 0), g.n) : g.n;
     a.hub_block_end =
-            g.by_degree ? first_below(g.prow, g.n, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
+            g.by_degree ? first_below(g.prow, a.gend, HOMLN_BLOCK_TIER_ITERS * (int64_t)(blockDim.x / Geo<W>::T)) : 0;
     a.hub_warp_end = g.by_degree
-                         ? max(a.hub_block_end, first_below(g.prow, g.n, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
+                         ? max(a.hub_block_end, first_below(g.prow, a.gend, HOMLN_WARP_TIER_ITERS * (32 / Geo<W>::T)))
                          : 0;
     a.rank = blockIdx.x;
     a.tsize = gridDim.x;
@@ -1110,6 +1125,8 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
         d.col = G.csr.col.p;
         d.prow = G.directed ? G.csr_in.rowptr.p : G.csr.rowptr.p;
         d.pcol = G.directed ? G.csr_in.col.p : G.csr.col.p;
+        d.split = G.relabeled ? G.split.p : nullptr;
+        d.pad = 0;
         if (G.relabeled) {
             if (!p->Fi[i].alloc(al, d.n) || !p->Ri[i].alloc(al, d.n)) fail(HOMLN_ENOMEM, "bfs relabelled outputs");
             d.F = p->Fi[i].p;
@@ -1269,16 +1286,17 @@ static void copy_csr(const Csr &g, Csr &out, Alloc *al, cudaStream_t s) {
 }
 
 void bfs_prepare(const Csr &g, const Csr *g_in, bool relabel, BfsGraph &out, Alloc *al, cudaStream_t s) {
-    // the vertex order follows the degrees of the graph the bottom-up levels read (in-edges)
+    // the vertex order follows the degrees of the graph the bottom-up levels read (in-edges);
+    // a directed graph's small components are the weak ones (in- and out-edges explored)
     out.relabeled = relabel;
     out.directed = g_in != nullptr;
     if (relabel) {
         DBuf<int32_t> inv;
         if (out.directed) {
-            relabel_by_degree(*g_in, out.csr_in, out.perm, inv, al, s);
+            relabel_by_degree(*g_in, &g, out.csr_in, out.perm, inv, out.split, al, s);
             relabel_apply(g, out.perm.p, inv.p, out.csr, al, s);
         } else {
-            relabel_by_degree(g, out.csr, out.perm, inv, al, s);
+            relabel_by_degree(g, nullptr, out.csr, out.perm, inv, out.split, al, s);
         }
     } else {  // the BFS reads the graph as it is
         copy_csr(g, out.csr, al, s);

@@ -306,6 +306,83 @@ def test_many_nodes_small_components(H):
     full_parity(H, net, sel, heuristics=(0, 2))
 
 
+def _scattered_components(n, seed, equal_giants=False):
+    """Edges of one graph whose components sit on random ids: a BA component (or two cycles of
+    equal size), a path, components right at the BFS's small-component bound (a path and a cycle
+    of 8 vertices, a star of 9), disjoint pairs, isolated vertices."""
+    rng = np.random.default_rng(seed)
+    ids = rng.permutation(n).astype(np.int32)
+    parts = []
+    if equal_giants:
+        k = n // 4
+        for off in (0, k):
+            c = np.arange(k)
+            parts.append((ids[off + c], ids[off + (c + 1) % k]))
+        used = 2 * k
+    else:
+        k = n // 2
+        s, d = synth.ba_edges(k, 3, seed)
+        parts.append((ids[s], ids[d]))
+        used = k
+    p = n // 6  # a path: the second largest component
+    parts.append((ids[used:used + p - 1], ids[used + 1:used + p]))
+    used += p
+    c = np.arange(8)
+    parts.append((ids[used + c[:-1]], ids[used + c[1:]]))  # path of 8
+    parts.append((ids[used + 8 + c], ids[used + 8 + (c + 1) % 8]))  # cycle of 8
+    parts.append((np.full(8, ids[used + 16]), ids[used + 17 + c]))  # star of 9
+    used += 25
+    q = n // 20  # disjoint pairs; the rest stays isolated
+    parts.append((ids[used:used + 2 * q:2], ids[used + 1:used + 2 * q:2]))
+    s = np.concatenate([a for a, _ in parts]).astype(np.int32)
+    d = np.concatenate([b for _, b in parts]).astype(np.int32)
+    return s, d
+
+
+@pytest.mark.parametrize("relabel", [1, 0])
+def test_component_split_of_the_batches(H, relabel):
+    """The BFS places the vertices of small components (at most 8 vertices) last and treats a
+    batch's sources on the other side of that split as unreachable: graphs whose components sit
+    on scattered ids, components at the bound, isolated vertices and pairs, each with and
+    without the relabelling, and the AND graph of such layers (components of its own)."""
+    n = 3001
+    layers = [_scattered_components(n, 41), _scattered_components(n, 42, equal_giants=True)]
+    shared = _scattered_components(n, 43)
+    layers.append((np.concatenate([shared[0], layers[0][0][: len(layers[0][0]) // 2]]),
+                   np.concatenate([shared[1], layers[0][1][: len(layers[0][1]) // 2]])))
+    net = synth.HoMLN(n, layers)
+    g = H.Network(n, to_dev(net.layers), tuning=dict(relabel=relabel, words_per_node=4))
+    ref = O.OracleHoMLN(n, net.layers, threads=8)
+    for i in range(len(layers)):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    for mask in (0b101, 0b111):
+        check_graph(*g.and_closeness(mask), ref.and_graph(mask))
+    g.close()
+
+
+def test_component_split_directed(H):
+    """Directed layers: weak components, and vertices without in-arcs (never reached)."""
+    n = 2500
+    rng = np.random.default_rng(44)
+    layers = []
+    for seed in (45, 46):
+        s, d = _scattered_components(n, seed)
+        flip = rng.random(s.size) < 0.5
+        s2, d2 = np.where(flip, d, s), np.where(flip, s, d)
+        src_only = rng.choice(n, 40, replace=False).astype(np.int32)  # arcs out of them only
+        tgt = rng.choice(n, 40).astype(np.int32)
+        keep = ~np.isin(d2, src_only)
+        layers.append((np.concatenate([s2[keep], src_only]).astype(np.int32),
+                       np.concatenate([d2[keep], tgt]).astype(np.int32)))
+    net = synth.HoMLN(n, layers)
+    g = H.Network(n, to_dev(net.layers), directed=True)
+    ref = O.OracleHoMLN(n, net.layers, threads=8, directed=True)
+    for i in range(len(layers)):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    check_graph(*g.and_closeness(0b11), ref.and_graph(0b11))
+    g.close()
+
+
 def test_path_and_cycle_closed_forms(H):
     """Long diameters (thousands of levels) against the closed forms directly."""
     n = 3000
