@@ -1012,12 +1012,14 @@ BfsKernel kernel_for(int W, bool stats) {
 
 // Widest tile: one team's state (3 arrays of n x W words) stays within this many bytes.
 constexpr double kWordsBudget = 104.0e6;
-// Default teams, measured on GB300 (W = 8, 304 blocks): 16 teams were best or within noise of
-// it on both the 50,000-node power-law workload (8 teams: 5% slower, 12: 1%, 24: equal) and
-// the 200,000-node BA workload (8-16 equal, 2 teams: 24% slower). The frontier gathers of
-// more teams than fit L2 still hit L2 mostly, and smaller teams meet at their barriers
-// sooner. The state of all teams is capped at kStateCap bytes.
+// Default teams: as many as keep the state of all teams near kTeamState bytes (about twice
+// L2), at least kDefaultTeams, and never more state than kStateCap bytes. Measured on GB300
+// (W = 8, 304 blocks): 24-25 teams at n = 50,000 (power-law: 16 teams 1.3% slower, 12 teams 4%,
+// 32 teams 1%), 16 at n = 200,000 (BA: 8-16 equal, 2 teams 24% slower), and for many graphs
+// of n <= 20,000 in one launch 60-76 teams (16 teams: 43% slower). The frontier gathers of
+// more teams than fit L2 still hit L2 mostly, and smaller teams meet at their barriers sooner.
 constexpr int kDefaultTeams = 16;
+constexpr double kTeamState = 2.4e8;
 constexpr double kStateCap = 2.0e9;
 
 }  // namespace
@@ -1070,7 +1072,7 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
     p->maxn = maxn;
     const bool plain = p->plain = t.schedule == 1;
     // teams and words per node: every team keeps its own state, and all of it should fit the budget
-    // Defaults, measured on GB300: 8 words per node (512 sources per tile), 16 teams.
+    // Defaults, measured on GB300: 8 words per node (512 sources per tile); teams as above.
     // The plain schedule (one team, the host driving every level) takes the widest tile the
     // budget allows, which needs the fewest launches and host round trips.
     const int W = p->W = t.W > 0 ? t.W : plain ? msbfs_pick_words(maxn) : std::min(8, msbfs_pick_words(maxn));
@@ -1079,8 +1081,9 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
         if (t.teams > 0) {
             nteams = t.teams;
         } else {
-            nteams = (int)std::floor(kStateCap / (3.0 * maxn * 8.0 * W));
-            nteams = std::max(1, std::min(kDefaultTeams, nteams));
+            const double per_team = 3.0 * maxn * 8.0 * W;  // bytes of one team's state
+            nteams = std::max(kDefaultTeams, (int)std::floor(kTeamState / per_team));
+            nteams = std::max(1, std::min(nteams, (int)std::floor(kStateCap / per_team)));
             int64_t tiles = 0;  // no more teams than tiles
             for (const BfsJob &j : jobs) tiles += ceil_div(j.g->csr.n, 64 * W);
             tiles = ceil_div(tiles, (int64_t)std::max(1, t.shard_world));
