@@ -132,7 +132,9 @@ typedef struct homln_tuning {
     int32_t threads;         /* threads per block of the persistent BFS (0 = 512) */
     int32_t blocks_per_sm;   /* resident blocks per SM (0 = as many as fit) */
     int32_t relabel;         /* 1 = degree-descending relabelling of each graph before BFS, 0 = off, -1 = default */
-    int32_t teams;           /* teams of blocks that run (graph, source batch) tiles concurrently (0 = auto) */
+    int32_t teams;           /* teams of blocks that run (graph, source batch) tiles concurrently (0 = auto:
+                                as many as keep the state of all teams near 240 MB, at least 16, at most
+                                one per tile and 2 GB of state in all) */
     int32_t team_mix;        /* 1: blocks resident on one SM join different teams; 0 (default): the same team */
     int32_t schedule;        /* 0 (default): one persistent launch over all (graph, batch) tiles;
                                 1: plain -- one ordinary launch per BFS phase, levels driven by the host
