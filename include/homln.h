@@ -300,7 +300,8 @@ HOMLN_API homln_status homln_accuracy(homln_t h, const int32_t *pred, int32_t n_
  * GPU's memory or because their loop must never enter an allocator; every handle-based call
  * allocates, so this one takes no handle).
  *   n_nodes      node universe, 1 <= n_nodes <= HOMLN_NOALLOC_MAX_NODES (larger: EINVAL).
- *   pred, truth  int32 node-id lists in DEVICE memory (host pointers: EINVAL); duplicates ignored.
+ *   pred, truth  int32 node-id lists in device memory of the CURRENT device, or managed memory
+ *                (host pointers, or another GPU's memory: EINVAL); duplicates ignored.
  *   stream       cudaStream_t to run on (NULL = legacy default stream).
  *   out          host output; the call synchronises `stream` before returning.
  * Same results as homln_accuracy. Scratch is one static device array (two 2^20-bit bitmaps

@@ -11,6 +11,7 @@
 // bitmaps of 2^15 words each plus a few counters (about 256 KB). Every GPU that
 // loads the library holds it until the process exits.
 #include "common.cuh"
+#include "devptr.h"
 
 #include <mutex>
 
@@ -53,13 +54,16 @@ void *scratch_address() {
     return g_addr[dev];
 }
 
-bool on_device(const void *p) {
+// True for device memory of the current device, or managed memory.
+bool on_current_device(const void *p) {
+    int dev = 0;
+    HCUDA(cudaGetDevice(&dev));
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return device_pointer_usable(at, dev);
 }
 
 }  // namespace
@@ -75,8 +79,9 @@ extern "C" homln_status homln_accuracy_noalloc(int32_t n_nodes, const int32_t *p
         if (n_nodes < 1 || n_nodes > HOMLN_NOALLOC_MAX_NODES)
             fail(HOMLN_EINVAL, "n_nodes must be in [1, HOMLN_NOALLOC_MAX_NODES = 2^20]");
         if (n_pred < 0 || n_truth < 0) fail(HOMLN_EINVAL, "negative list length");
-        if ((n_pred > 0 && (!pred || !on_device(pred))) || (n_truth > 0 && (!truth || !on_device(truth))))
-            fail(HOMLN_EINVAL, "pred and truth must be device memory");
+        if ((n_pred > 0 && (!pred || !on_current_device(pred))) ||
+            (n_truth > 0 && (!truth || !on_current_device(truth))))
+            fail(HOMLN_EINVAL, "pred and truth must be device memory of the current device");
         cudaStream_t s = (cudaStream_t)stream;
         unsigned long long *base = static_cast<unsigned long long *>(scratch_address());
         homln_accuracy_t r;

@@ -318,7 +318,11 @@ def homln_accuracy(h, pred, n_pred: int, truth, n_truth: int) -> dict:
 
 
 def homln_accuracy_noalloc(n_nodes: int, pred, n_pred: int, truth, n_truth: int, stream=None) -> dict:
-    """Accuracy for callers that cannot allocate device memory: pred/truth must be device memory."""
+    """Accuracy for callers that cannot allocate device memory: pred/truth must be device memory of
+    the current device. stream=None runs on torch's current stream (so inputs written there are ready)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
     out = homln_accuracy_t()
     _check(lib.homln_accuracy_noalloc(int(n_nodes), ptr(pred), int(n_pred), ptr(truth), int(n_truth),
                                       c_void_p(stream) if stream else None, ctypes.byref(out)),

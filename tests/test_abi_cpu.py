@@ -71,3 +71,44 @@ def test_create_without_device_reports_cuda_error(H):
     with pytest.raises(H.HomlnError) as e:
         H.homln_create(3, [(s, d)])
     assert e.value.code in (H.HOMLN_ECUDA, H.HOMLN_ENOMEM)
+
+
+def test_noalloc_pointer_rule_without_gpu(tmp_path):
+    """homln_accuracy_noalloc reads its id lists in kernels on the current device, so it accepts only
+    managed memory and device memory of that device; another GPU's memory (no peer access) and host
+    memory are refused with EINVAL. The rule is plain C++ over cudaPointerAttributes, checked here
+    with faked attributes."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    inc = "/usr/local/cuda/include"
+    if not gxx or not os.path.exists(os.path.join(inc, "cuda_runtime_api.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    src = tmp_path / "rule.cpp"
+    src.write_text(r'''
+#include "devptr.h"
+#include <cstdio>
+static cudaPointerAttributes attr(cudaMemoryType t, int dev) {
+    cudaPointerAttributes a{};
+    a.type = t;
+    a.device = dev;
+    return a;
+}
+int main() {
+    using homln::device_pointer_usable;
+    int bad = 0;
+    bad += !device_pointer_usable(attr(cudaMemoryTypeDevice, 0), 0);   // this GPU
+    bad += !device_pointer_usable(attr(cudaMemoryTypeDevice, 3), 3);
+    bad += device_pointer_usable(attr(cudaMemoryTypeDevice, 1), 0);    // another GPU
+    bad += device_pointer_usable(attr(cudaMemoryTypeDevice, 0), 2);
+    bad += !device_pointer_usable(attr(cudaMemoryTypeManaged, 1), 0);  // managed: any device
+    bad += device_pointer_usable(attr(cudaMemoryTypeHost, 0), 0);      // pinned host
+    bad += device_pointer_usable(attr(cudaMemoryTypeUnregistered, 0), 0);
+    std::printf("%d\n", bad);
+    return bad;
+}
+''')
+    exe = tmp_path / "rule"
+    subprocess.check_call([gxx, "-std=c++17", "-I", inc, "-I", os.path.join(ROOT, "paper_2207_11662_gb300", "csrc"),
+                           str(src), "-o", str(exe)])
+    assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "0"
