@@ -148,6 +148,10 @@ typedef struct homln_tuning {
                                 per launch and launches again for the rest, so that work on other
                                 streams (e.g. a higher-priority one) can run in between; identical
                                 results (0 = all tiles in one launch) */
+    int32_t sm_count;        /* the persistent BFS launches blocks_per_sm x sm_count blocks, so that it
+                                occupies about sm_count SMs' worth of the GPU and work on other streams
+                                (another request's analysis, say) runs beside it on the rest;
+                                identical results (0 = every SM; larger than the device: every SM) */
 } homln_tuning;
 
 /* Create a handle: copy the layers to the device and build one CSR per layer.

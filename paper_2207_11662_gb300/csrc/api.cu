@@ -726,6 +726,8 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         bt.phantom = t->test_phantom_blocks;
         if (t->max_tiles_per_launch < 0) fail(HOMLN_EINVAL, "max_tiles_per_launch must be >= 0");
         bt.max_tiles = t->max_tiles_per_launch;
+        if (t->sm_count < 0) fail(HOMLN_EINVAL, "sm_count must be >= 0");
+        bt.sm_count = t->sm_count;
     }
     h->tuning = bt;
     API_END

@@ -268,6 +268,7 @@ struct BfsTuning {
     int wait_limit_ms = 2000;  // device-side waits give up after this long (HOMLN_ETIMEOUT)
     int phantom = 0;           // tests: team barriers also wait for blocks that do not exist
     int max_tiles = 0;         // persistent launches take at most this many tiles each (0 = all)
+    int sm_count = 0;          // persistent launches size their grid for this many SMs (0 = all)
     int shard_rank = 0;        // only source batches shard_rank, shard_rank + shard_world, ...
     int shard_world = 1;       //   (partial F/R of a sharded analysis; 0 / 1 = all sources)
 };

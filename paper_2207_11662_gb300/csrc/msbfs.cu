@@ -284,21 +284,26 @@ __device__ __forceinline__ bool id_ok(const Tile &a, int64_t u) {
     return false;
 }
 
+// Column indices of the neighbours rb+p, rb+p+S, ... (kUnroll of them; -1 past the row end re).
+__device__ __forceinline__ void load_cols(const Tile &a, int64_t j, int64_t re, int S, int32_t (&u)[kUnroll]) {
+#pragma unroll
+    for (int i = 0; i < kUnroll; ++i) u[i] = (j + (int64_t)i * S < re) ? __ldg(a.pcol + j + (int64_t)i * S) : -1;
+}
+
 // OR the frontier words (this lane's K of them) of neighbours rb+p, rb+p+S, ... into acc;
 // stop once every bit this lane still needs is present. kUnroll neighbours are gathered per
 // step (past the row end the loads are predicated off), and the column indices of the next
-// step are loaded while the current frontier words are in flight. Returns neighbours visited.
+// step are loaded while the current frontier words are in flight. u holds the first step's
+// column indices (load_cols(a, rb + p, re, S, u)), loaded by the caller so that they can be in
+// flight before the caller knows whether the vertex needs any bit. Returns neighbours visited.
 template <int W>
 __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__restrict__ cur, int64_t rb, int64_t re,
-                                             int p, int S, int q, const uint64_t (&need)[Geo<W>::K],
-                                             uint64_t (&acc)[Geo<W>::K]) {
+                                             int p, int S, int q, int32_t (&u)[kUnroll],
+                                             const uint64_t (&need)[Geo<W>::K], uint64_t (&acc)[Geo<W>::K]) {
     constexpr int K = Geo<W>::K, U = kUnroll;
     int64_t j = rb + p;
     if (j >= re) return 0;
     int64_t it = 0;
-    int32_t u[U];
-#pragma unroll
-    for (int i = 0; i < U; ++i) u[i] = (j + (int64_t)i * S < re) ? __ldg(a.pcol + j + (int64_t)i * S) : -1;
     while (true) {
         uint64_t f[U][K];
 #pragma unroll
@@ -313,10 +318,7 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
         const int64_t jn = j + (int64_t)U * S;
         const bool more = jn < re;
         const int64_t here = (min(re, jn) - j + S - 1) / S;
-        if (more) {
-#pragma unroll
-            for (int i = 0; i < U; ++i) u[i] = (jn + (int64_t)i * S < re) ? __ldg(a.pcol + jn + (int64_t)i * S) : -1;
-        }
+        if (more) load_cols(a, jn, re, S, u);
 #pragma unroll
         for (int i = 0; i < U; ++i)
 #pragma unroll
@@ -583,7 +585,11 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             }
             const int64_t rb = a.prow[v], re = a.prow[v + 1];
             int64_t it = 0;
-            if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
+            if (lane_need) {
+                int32_t u[kUnroll];
+                load_cols(a, rb + p, re, S, u);
+                it = gather_or<W>(a, cur, rb, re, p, S, q, u, need, acc);
+            }
             if (STATS) {
                 st[ST_WORDS] += it * K;
                 st[ST_BYTES] += it * 8 * K;
@@ -616,7 +622,10 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
     }
     // --- warp tier: hubs below the block threshold, all slots of a warp share one row
     {
-        const int S = 32 / T, p = lane / T;
+        const int p = lane / T;
+#if !HOMLN_WARP_COORD
+        const int S = 32 / T;
+#endif
         const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
         const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
         for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) {
@@ -638,7 +647,11 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
 #if HOMLN_WARP_COORD
             if (!full0) it = gather_or_warp<W>(a, cur, rb, re, q, need, acc);
 #else
-            if (lane_need) it = gather_or<W>(a, cur, rb, re, p, S, q, need, acc);
+            if (lane_need) {
+                int32_t u[kUnroll];
+                load_cols(a, rb + p, re, S, u);
+                it = gather_or<W>(a, cur, rb, re, p, S, q, u, need, acc);
+            }
 #endif
             if (STATS) {
                 st[ST_WORDS] += it * K;
@@ -656,45 +669,56 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, c, st);
         }
     }
-    // --- group tier: T lanes per vertex. Warps take chunks of vertices from the team's work
-    // counter, so a slow vertex (no early exit, long row) delays only its own chunk.
+    // --- group tier: T lanes per vertex. Warps take chunks of consecutive vertices from the
+    // team's work counter, so a slow vertex (no early exit, long row) delays only its own chunk.
+    // A chunk's row bounds and quiet bytes are read once, coalesced, and handed to the passes by
+    // shuffles; the warp's next chunk is reserved while the current one runs. A pass then waits
+    // for one load (seen words and the first column indices, issued together) before its
+    // frontier gathers, instead of three in a row.
     {
         unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
-        const int64_t per_pass = 32 / T;
-        const int64_t chunk = per_pass * kChunkPasses;
+        constexpr int per_pass = 32 / T;
+        constexpr int chunk = per_pass * kChunkPasses < 32 ? per_pass * kChunkPasses : 32;
         const int64_t nrest = a.n - a.hub_warp_end;
+        long long next = 0;
+        if (lane == 0) next = (long long)atomicAdd(work, (unsigned long long)chunk);
         for (;;) {
-            long long base = 0;
-            if (lane == 0) base = (long long)atomicAdd(work, (unsigned long long)chunk);
-            base = __shfl_sync(0xffffffffu, base, 0);
+            const long long base = __shfl_sync(0xffffffffu, next, 0);
             if (base >= nrest) break;  // uniform over the warp
-            const int64_t vend = a.hub_warp_end + min((int64_t)base + chunk, nrest);
-            int64_t v = a.hub_warp_end + base + lane / T;
-            // the next pass's quiet byte is loaded while this pass runs (one dependent load less
-            // per vertex; measured 1.2% faster; prefetching the row bounds too spilled and was slower)
-            uint8_t q_next = v < vend ? a.quiet[v] : 0;
-            for (; __any_sync(0xffffffffu, v < vend); v += per_pass) {
-                const uint8_t qv = q_next;
-                q_next = v + per_pass < vend ? a.quiet[v + per_pass] : 0;
-                if (STATS && q == 0 && v < vend) st[ST_BYTES] += 1;
-                const bool act = v < vend && qv < QUIET;
+            if (lane == 0) next = (long long)atomicAdd(work, (unsigned long long)chunk);
+            const int64_t v0 = a.hub_warp_end + base;
+            const int cnt = (int)min((int64_t)chunk, (int64_t)(nrest - base));  // vertices of this chunk
+            // lane i holds vertex v0+i's row bounds and quiet byte (i < cnt)
+            const int64_t rb_l = a.prow[v0 + min(lane, cnt)];
+            const int64_t re_l = a.prow[v0 + min(lane + 1, cnt)];
+            const int q_l = lane < cnt ? (int)a.quiet[v0 + lane] : (int)QUIET;
+            for (int pass = 0; pass * per_pass < cnt; ++pass) {  // uniform over the warp
+                const int i = pass * per_pass + lane / T;
+                const int64_t v = v0 + i;
+                const int qv = __shfl_sync(0xffffffffu, q_l, i & 31);
+                const int64_t rb0 = __shfl_sync(0xffffffffu, (long long)rb_l, i & 31);
+                const int64_t re0 = __shfl_sync(0xffffffffu, (long long)re_l, i & 31);
+                if (STATS && q == 0 && i < cnt) st[ST_BYTES] += 1;
+                const bool act = i < cnt && qv < QUIET;
                 uint64_t s[K], need[K], acc[K], nw[K];
+                int32_t u[kUnroll];
                 bool lane_need = false;
                 int64_t rb = 0, re = 0;
 #pragma unroll
                 for (int k = 0; k < K; ++k) s[k] = need[k] = acc[k] = 0;
                 if (act) {
+                    rb = rb0;
+                    re = re0;
                     ldw<K>(a.seen + v * W + q * K, s);
+                    load_cols(a, rb, re, 1, u);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         need[k] = ~s[k];
                         lane_need |= need[k] != 0;
                     }
-                    rb = a.prow[v];
-                    re = a.prow[v + 1];
                 }
                 int64_t it = 0;
-                if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, need, acc);
+                if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, u, need, acc);
                 if (STATS) {
                     st[ST_WORDS] += it * K;
                     st[ST_BYTES] += it * 8 * K;
@@ -1100,7 +1124,9 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
     HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
-    const int grid = p->grid = nsm * per_sm;
+    // sm_count: a grid for that many SMs' worth of blocks leaves the rest of the GPU to other streams
+    const int use_sm = t.sm_count > 0 ? std::min(nsm, t.sm_count) : nsm;
+    const int grid = p->grid = use_sm * per_sm;
     if (nteams > grid) nteams = grid;
     p->nteams = nteams;
     p->nsm = nsm;

@@ -61,7 +61,7 @@ class homln_tuning(ctypes.Structure):
     _fields_ = [("words_per_node", c_int32), ("push_alpha", c_int32), ("threads", c_int32),
                 ("blocks_per_sm", c_int32), ("relabel", c_int32), ("teams", c_int32), ("team_mix", c_int32),
                 ("schedule", c_int32), ("wait_limit_ms", c_int32), ("test_phantom_blocks", c_int32),
-                ("max_tiles_per_launch", c_int32)]
+                ("max_tiles_per_launch", c_int32), ("sm_count", c_int32)]
 
 
 class homln_profile_t(ctypes.Structure):
@@ -214,9 +214,9 @@ def homln_destroy(h) -> None:
 
 def homln_set_tuning(h, words_per_node=0, push_alpha=0, threads=0, blocks_per_sm=0, relabel=-1, teams=0,
                      team_mix=0, schedule=0, wait_limit_ms=0, test_phantom_blocks=0,
-                     max_tiles_per_launch=0) -> None:
+                     max_tiles_per_launch=0, sm_count=0) -> None:
     t = homln_tuning(words_per_node, push_alpha, threads, blocks_per_sm, relabel, teams, team_mix, schedule,
-                     wait_limit_ms, test_phantom_blocks, max_tiles_per_launch)
+                     wait_limit_ms, test_phantom_blocks, max_tiles_per_launch, sm_count)
     _check(lib.homln_set_tuning(h, ctypes.byref(t)), "homln_set_tuning")
 
 
