@@ -1,32 +1,51 @@
 """Autotuner for the persistent multi-source BFS.
 
-Picks the team count, the words per node W (64*W sources per tile) and the
+Picks the words per node W (64*W sources per tile), the team count and the
 top-down threshold alpha for a set of graphs by timing real launches of
-homln_batch_analyse on the GPU. Results are cached per workload class (graph
-count, largest node count and edge count, bucketed) in a JSON file under the
-build directory, so a serving process or a benchmark tunes once.
+homln_batch_analyse on the GPU. The search is coordinate-wise: W first (teams
+and alpha at the library's defaults), then the team count at the best W, then
+alpha at the best (W, teams). Every candidate is timed ``reps`` times (at
+least 3) and scored by its median. Results are cached per workload class
+(graph count, largest node count, total edges and degree skew, each bucketed
+to a power of two) in a JSON file under the build directory, so a serving
+process or a benchmark tunes once.
 """
 from __future__ import annotations
 
 import json
 import math
 import os
+import statistics
 
 from . import homln as H
 
 _CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "autotune.json")
 
-# (teams, words per node, alpha); W = 0 lets the library size W to its state budget
-DEFAULT_CANDIDATES = [
-    (8, 0, 16), (4, 0, 16), (16, 0, 16), (32, 0, 16), (76, 0, 16), (152, 0, 16),
-    (8, 0, 32), (16, 0, 4), (32, 0, 4),
-]
+WORDS = (4, 8, 16, 32)           # 256 .. 2048 sources per tile
+TEAMS = (0, 4, 8, 16, 32, 76, 152)  # 0: the library's default for the chosen W
+ALPHAS = (4, 16, 64)             # top-down while alpha * frontier edges < unfinished edges
+STATE_LIMIT = 2.0e9              # bytes of BFS state a candidate may take (3 arrays of n x W words per team)
 
 
-def workload_key(ns, edges) -> str:
-    """Bucket a workload: graph count, largest n and total edges, each to a power of two."""
+def workload_key(ns, edges, skew: float = 1.0) -> str:
+    """Bucket a workload: graph count, largest n, total edges and degree skew (max / mean degree),
+    each to a power of two."""
     b = lambda x: int(math.log2(max(int(x), 1)))
-    return f"g{b(len(ns))}-n{b(max(ns))}-e{b(sum(edges))}"
+    return f"g{b(len(ns))}-n{b(max(ns))}-e{b(sum(edges))}-s{b(skew)}"
+
+
+def degree_skew(n: int, layers) -> float:
+    """Largest max-degree / mean-degree ratio over the layers of one network (edge lists as given)."""
+    import numpy as np
+    worst = 1.0
+    for s, d in layers:
+        s = np.asarray(s)
+        d = np.asarray(d)
+        if s.size == 0:
+            continue
+        deg = np.bincount(np.concatenate([s, d]), minlength=n)
+        worst = max(worst, float(deg.max()) / max(float(deg.mean()), 1e-9))
+    return worst
 
 
 def _load():
@@ -45,12 +64,12 @@ def _store(cache):
     os.replace(tmp, _CACHE)
 
 
-def time_batch(handles, masks, with_and, stream_ptr: int, tuning: dict, reps: int = 1) -> float:
-    """Milliseconds of one homln_batch_analyse (best of reps), CUDA events on the launch stream."""
+def time_batch(handles, masks, with_and, stream_ptr: int, tuning: dict, reps: int = 3) -> float:
+    """Median milliseconds of homln_batch_analyse over reps runs, CUDA events on the launch stream."""
     import torch
     stream = torch.cuda.ExternalStream(stream_ptr) if stream_ptr else torch.cuda.current_stream()
     H.homln_set_tuning(handles[0], **tuning)
-    best = float("inf")
+    times = []
     for _ in range(reps):
         for h in handles:
             H.homln_invalidate(h)
@@ -61,29 +80,44 @@ def time_batch(handles, masks, with_and, stream_ptr: int, tuning: dict, reps: in
         H.homln_batch_analyse(handles, masks, with_and)
         e1.record(stream)
         e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    return best
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
 
 
-def tune(handles, masks, ns, edges, with_and=True, stream_ptr: int = 0, candidates=None, use_cache=True,
-         reps: int = 1):
-    """Best tuning dict for this set of graphs (and the timings of every candidate)."""
-    key = workload_key(ns, edges)
+def tune(handles, masks, ns, edges, with_and=True, stream_ptr: int = 0, use_cache=True, reps: int = 3,
+         skew: float = 1.0, words=WORDS, teams=TEAMS, alphas=ALPHAS):
+    """Best tuning dict for this set of graphs, and a log of every candidate timed."""
+    reps = max(3, int(reps))
+    key = workload_key(ns, edges, skew)
     cache = _load() if use_cache else {}
     if key in cache:
         return cache[key]["tuning"], cache[key]
-    results = []
+    maxn = max(ns)
     time_batch(handles, masks, with_and, stream_ptr, {}, 1)  # untimed: builds the BFS graphs once
-    for teams, words, alpha in candidates or DEFAULT_CANDIDATES:
-        t = dict(teams=teams, words_per_node=words, push_alpha=alpha)
-        try:
-            ms = time_batch(handles, masks, with_and, stream_ptr, t, reps)
-        except H.HomlnError:
-            continue
-        results.append((ms, t))
+    results = []
+    seen = {}
+
+    def run(t):
+        k = tuple(sorted(t.items()))
+        if k not in seen:
+            try:
+                seen[k] = time_batch(handles, masks, with_and, stream_ptr, t, reps)
+            except H.HomlnError:
+                seen[k] = float("inf")
+            results.append((seen[k], dict(t)))
+        return seen[k]
+
+    # W: no wider than the node count needs, one team's state within the limit
+    ws = [w for w in words if 64 * (w // 2) < maxn and 3.0 * maxn * 8.0 * w <= STATE_LIMIT] or [1]
+    best = min(({"words_per_node": w, "teams": 0, "push_alpha": 16} for w in ws), key=run)
+    tiles = sum(-(-n // (64 * best["words_per_node"])) for n in ns)
+    per_team = 3.0 * maxn * 8.0 * best["words_per_node"]
+    tcands = [t for t in teams if t == 0 or (t <= tiles and t * per_team <= STATE_LIMIT)]
+    best = min((dict(best, teams=t) for t in tcands), key=run)
+    best = min((dict(best, push_alpha=a) for a in alphas), key=run)
     results.sort(key=lambda x: x[0])
-    best = results[0][1]
-    entry = {"tuning": best, "candidates": [{"ms": round(ms, 3), **t} for ms, t in results]}
+    entry = {"tuning": best, "key": key, "reps": reps,
+             "candidates": [{"ms": round(ms, 3), **t} for ms, t in results]}
     if use_cache:
         cache[key] = entry
         _store(cache)
