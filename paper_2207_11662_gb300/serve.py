@@ -11,21 +11,18 @@ Scheduling:
     a request that can never fit is rejected (HOMLN_ENOMEM) at once;
   * continuous batching: worker threads, each with its own CUDA stream, repeatedly
     take admitted requests that are waiting (up to ``max_wave``) and run them as one
-    wave: CSR builds, then persistent BFS launches over all (graph, source batch)
-    tiles of the wave (homln_batch_analyse) on the whole GPU, then selection,
-    composition and accuracy. Requests that arrive while a wave is on the GPU join
-    the next wave of a free worker;
-  * size classes: a request is "big" when its BFS work (nodes x edges) exceeds
-    ``big_work``. One worker (the default) takes waves in arrival order across the
-    classes. With two or more workers, one serves only small requests on a
-    high-priority stream; the others take big requests first (then small ones) on
-    low-priority streams and split a big wave's BFS into launches of at most
-    ``big_max_tiles`` tiles, so that the GPU can take up small waves between them.
-    Measured on GB300 at 50 requests/s (config 5): one worker p50 8.4-9.0 ms / p99
-    119-122 ms; two workers in arrival order 9.0 / 127 ms; the class split with two
-    workers 10.4-14.9 / 136-183 ms (smaller launches were worse); three workers whose
-    waves took one block per SM each 26 / 326 ms. The largest requests' own service
-    time (up to ~4e11 edge visits) sets the p99.
+    wave: CSR builds, then one persistent BFS launch over all (graph, source batch)
+    tiles of the wave (homln_batch_analyse), then selection, composition and
+    accuracy. Requests that arrive while a wave is on the GPU join the next wave of
+    a free worker;
+  * size classes and overlap on the device: a request is "big" when its BFS work
+    (nodes x edges) exceeds ``big_work``. With two or more workers (the default is
+    two), worker 0 serves only small requests, on a high-priority stream, and its
+    persistent BFS launches are sized for ``small_sms`` SMs; the other workers take
+    big requests first (then small ones) and size theirs for the remaining SMs. So a
+    small request that arrives while a big one is on the GPU starts at once: its
+    kernels run beside the big request's BFS instead of waiting for it to end.
+    With one worker every wave takes the whole GPU, in arrival order.
 
 Every GPU step runs in libhomln.so; this module only schedules.
 """
@@ -157,15 +154,17 @@ def work_estimate(n: int, edge_counts) -> int:
 
 
 class Server:
-    def __init__(self, device: int = 0, workers: int = 1, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
+    def __init__(self, device: int = 0, workers: int = 2, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
                  percent: float = 10.0, keep_farness: bool = False, tuning: dict | None = None,
-                 big_work: float = 2e10, big_max_tiles: int = 64):
+                 big_work: float = 2e10, small_sms: int = 32, big_max_tiles: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.workers = workers
         self.max_wave = max_wave
         self.big_work = big_work
+        self.nsm = torch.cuda.get_device_properties(self.device).multi_processor_count
+        self.small_sms = max(1, min(int(small_sms), self.nsm - 1))
         self.big_max_tiles = big_max_tiles
         self.adm = Admission(mem_budget_bytes)
         self.sel = H.make_select(H.HOMLN_TOPK_PERCENT, percent)
@@ -223,14 +222,16 @@ class Server:
     def _worker(self, idx):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        # worker 0 of two or more serves small requests only, at high priority; the others take
-        # big requests first, at low priority, with their BFS split into launches
+        # worker 0 of two or more serves small requests only, at high priority, on small_sms SMs'
+        # worth of BFS blocks; the others take big requests first on the rest of the GPU
         small_only = self.workers >= 2 and idx == 0
         classes = (SMALL,) if small_only else (BIG, SMALL) if self.workers >= 2 else None
         stream = torch.cuda.Stream(self.device, priority=-1 if small_only else 0)
         tuning = dict(self.tuning)
-        if not small_only and self.workers >= 2:
-            tuning.setdefault("max_tiles_per_launch", self.big_max_tiles)
+        if self.workers >= 2:
+            tuning.setdefault("sm_count", self.small_sms if small_only else self.nsm - self.small_sms)
+            if not small_only and self.big_max_tiles:
+                tuning.setdefault("max_tiles_per_launch", self.big_max_tiles)
         while True:
             items = self.adm.take(self.max_wave, timeout=0.05, classes=classes)
             if items is None:
@@ -276,10 +277,25 @@ class Server:
         return sorted(self.done, key=lambda r: r.rid)
 
 
-def latency_stats(done, wall_s: float) -> dict:
+def latency_stats(done, wall_s: float, big_work: float = 2e10) -> dict:
+    """Latency (completion - arrival) percentiles over the completed requests, overall and per size
+    class (BFS work nodes x edges above or below big_work)."""
     ok = [r for r in done if r.status == H.HOMLN_OK]
-    lat = np.array([(r.t_done - r.arrival) * 1000.0 for r in ok]) if ok else np.zeros(1)
-    return {"requests": len(done), "completed": len(ok), "rejected": len(done) - len(ok),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "mean_ms": round(float(lat.mean()), 3), "req_per_s": round(len(ok) / wall_s, 2),
-            "gteps": round(sum(r.teps_work for r in ok) / wall_s / 1e9, 2)}
+
+    def pct(rs):
+        lat = np.array([(r.t_done - r.arrival) * 1000.0 for r in rs]) if rs else np.zeros(1)
+        return lat
+
+    lat = pct(ok)
+    big = [r for r in ok if work_estimate(r.n, [s.shape[0] for s, _ in r.layers]) > big_work]
+    small = [r for r in ok if r not in big]
+    out = {"requests": len(done), "completed": len(ok), "rejected": len(done) - len(ok),
+           "p50_ms": round(float(np.percentile(lat, 50)), 3), "p90_ms": round(float(np.percentile(lat, 90)), 3),
+           "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "mean_ms": round(float(lat.mean()), 3), "req_per_s": round(len(ok) / wall_s, 2),
+           "gteps": round(sum(r.teps_work for r in ok) / wall_s / 1e9, 2)}
+    for name, rs in (("small", small), ("big", big)):
+        la = pct(rs)
+        out[name] = {"count": len(rs), "p50_ms": round(float(np.percentile(la, 50)), 3),
+                     "p99_ms": round(float(np.percentile(la, 99)), 3)}
+    return out
