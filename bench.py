@@ -5,14 +5,17 @@ One step = one pass of the whole hot path over one HoMLN:
   AND aggregation + all-sources BFS closeness of the AND graph (ground truth) ->
   top-10% CC nodes -> naive, CC1 and CC2 composition (Theta) -> accuracy of each.
 
-Workload (default): 4 Chung-Lu power-law layers (exponent 2.5, average degree 10)
-on 50,000 shared nodes with a shared edge pool of rho*m edges, rho ~ U[0.3, 0.7]
-(seeded synthetic stand-in for the paper's RMAT/PaRMAT HoMLNs).
+Workload (default, the largest single-GPU configuration): 4 Barabasi-Albert layers
+(m = 4) on 200,000 shared nodes, half of one base BA graph shared by every layer
+(seeded synthetic stand-in for the paper's RMAT/PaRMAT HoMLNs). The 4-layer
+Chung-Lu n = 50,000 workload is measured beside it (``configs``), as are the
+batched 64-network workload and the serving stream.
 
 Metric: GTEPS = sum over the analysed graphs of sum_s |E(component(s))| / time
 (Graph500 convention for all-sources BFS), whole job over all ranks.
 
-Prints one JSON line (rank 0).
+Prints one JSON line (rank 0); its last key, ``summary``, repeats the headline
+figures, the batched-vs-plain speedup and the serving latencies in a few fields.
 """
 from __future__ import annotations
 
@@ -40,9 +43,12 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="powerlaw50k", choices=["powerlaw50k", "ba200k", "er1k"])
+    p.add_argument("--workload", default="ba200k", choices=["powerlaw50k", "ba200k", "er1k"])
+    p.add_argument("--secondary", default="powerlaw50k", choices=["powerlaw50k", "ba200k", "er1k", "none"],
+                   help="another configuration measured beside the headline (none: skip)")
+    p.add_argument("--no-autotune", action="store_true", help="library defaults instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-sources", type=int, default=1500)
+    p.add_argument("--cpu-sample-sources", type=int, default=2000)
     p.add_argument("--words", type=int, default=0, help="BFS words per node (0 = auto)")
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--teams", type=int, default=0, help="BFS teams (0 = auto)")
@@ -187,26 +193,32 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def measured_traffic(workload: str, tiles: int):
-    """DRAM bytes per BFS launch from the committed ncu summary (profiles/), scaled from the captured
-    tiles to this launch's tiles; None when the kernel source changed since the counters were taken."""
+PROFILE_FILES = {"powerlaw50k": "k_msbfs_powerlaw50k_launch.md", "ba200k": "k_msbfs_ba200k_launch.md"}
+
+
+def measured_traffic(workload: str, tiles: int, words: int, teams: int):
+    """DRAM bytes (read + write) per BFS launch from the committed ncu summary under profiles/,
+    scaled from the captured launch's tiles to this launch's; None when the kernel source, the
+    words per node or the team count differ from the capture's."""
     import hashlib
-    if workload != "powerlaw50k":
+    if workload not in PROFILE_FILES:
         return None
-    path = os.path.join(ROOT, "profiles", "k_msbfs_powerlaw50k_layer.md")
+    path = os.path.join(ROOT, "profiles", PROFILE_FILES[workload])
     src = os.path.join(ROOT, "paper_2207_11662_gb300", "csrc", "msbfs.cu")
     try:
         kv = {}
         with open(path) as f:
             for line in f:
-                if ":" in line and not line.startswith(("|", "#", "`")):
+                if ":" in line and not line.startswith(("|", "#", "`", " ")):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
         with open(src, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
         if kv.get("kernel_source_sha256_16") != sha:
             return None
-        return int(int(kv["dram_bytes_per_tile"]) * tiles)
+        if int(kv["words_per_node"]) != int(words) or int(kv["teams"]) != int(teams):
+            return None
+        return int(int(kv["dram_bytes_launch"]) * tiles / int(kv["tiles_in_capture"]))
     except (OSError, KeyError, ValueError):
         return None
 
@@ -219,6 +231,137 @@ def bfs_bytes(prof: dict) -> float:
     return float(prof["bytes"])
 
 
+def tuning_from_args(args) -> dict:
+    t = {}
+    if args.words:
+        t["words_per_node"] = args.words
+    if args.alpha:
+        t["push_alpha"] = args.alpha
+    if args.teams:
+        t["teams"] = args.teams
+    if args.team_mix:
+        t["team_mix"] = 1
+    if args.threads:
+        t["threads"] = args.threads
+    return t
+
+
+class HotPath:
+    """One step of the hot path on one HoMLN through the binding: create (CSR builds), Psi of every
+    layer and the AND graph in one persistent launch, closeness read-back, AND edge count, top-10%
+    ground truth, naive/CC1/CC2 and the accuracy of each."""
+
+    def __init__(self, H, net, dev, stream, tuning):
+        self.H, self.net, self.dev, self.stream, self.tuning = H, net, dev, stream, dict(tuning)
+        self.sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
+
+    def step(self, layers, host_out=False, profile=None):
+        import torch
+        H, n, L = self.H, self.net.n, self.net.n_layers
+        full = (1 << L) - 1
+        h = H.homln_create(n, layers, stream=self.stream.cuda_stream)
+        try:
+            if self.tuning:
+                H.homln_set_tuning(h, **self.tuning)
+            if profile is not None:
+                H.homln_set_profiling(h, profile == "time", profile == "count")
+            if host_out:
+                F = np.empty(n, np.uint64)
+                R = np.empty(n, np.uint32)
+                cc = np.empty(n, np.float64)
+                ids = [np.empty(n, np.int32) for _ in range(4)]
+            else:
+                F = torch.empty(n, dtype=torch.int64, device=self.dev)
+                R = torch.empty(n, dtype=torch.int32, device=self.dev)
+                cc = torch.empty(n, dtype=torch.float64, device=self.dev)
+                ids = [torch.empty(n, dtype=torch.int32, device=self.dev) for _ in range(4)]
+            H.homln_analyse(h, full, True)  # Psi of every layer and the AND graph in one launch
+            for i in range(L):
+                H.homln_layer_closeness(h, i, F, R, cc)
+            m_and = H.homln_and_aggregate(h, full)
+            H.homln_and_closeness(h, full, F, R, cc)
+            cg = H.homln_topk(h, -1, full, self.sel, ids[0])
+            accs = []
+            for j, heur in enumerate((H.HOMLN_NAIVE, H.HOMLN_CC1, H.HOMLN_CC2)):
+                c = H.homln_compose(h, full, heur, self.sel, ids[j + 1])
+                accs.append(H.homln_accuracy(h, ids[j + 1], c, ids[0], cg))
+            prof = H.homln_get_profile(h) if profile is not None else None
+            return accs, prof, m_and
+        finally:
+            H.homln_destroy(h)
+
+
+def autotune_workload(H, net, dev, stream, reps=3):
+    """The autotuner's pick (W, teams, alpha) for this network's analysis (every layer + AND)."""
+    import torch
+    from paper_2207_11662_gb300 import autotune
+    n, L = net.n, net.n_layers
+    layers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
+    h = H.homln_create(n, layers, stream=stream.cuda_stream)
+    try:
+        edges = [int(s.shape[0]) for s, _ in net.layers]
+        best, log = autotune.tune([h], [(1 << L) - 1], [n], edges, True, stream.cuda_stream, use_cache=False,
+                                  reps=reps, skew=autotune.degree_skew(n, net.layers))
+    finally:
+        H.homln_destroy(h)
+    return best, log
+
+
+def measure(H, hp: HotPath, dev, steps, warmup, flush, dist=None, sample_clocks=False):
+    """Warm-up, one untimed instrumented pass (the BFS kernel's algorithmic bytes), then `steps` timed
+    steps on device-resident inputs with L2 flushed before each; CUDA events on the launch stream."""
+    import torch
+    net, stream = hp.net, hp.stream
+    dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
+    for _ in range(warmup):
+        hp.step(dlayers)
+    torch.cuda.synchronize()
+    _, prof_count, m_and = hp.step(dlayers, profile="count")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = H.homln_kernel_launches()
+    bfs_ms, bfs_launches = 0.0, 0
+    accs = None
+    clk = ClockSampler(dev.index) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    try:
+        for k in range(steps):
+            flush.fill_(k)  # evict L2 between steps (512 MB > 129 MB)
+            ev[k][0].record(stream)
+            accs, prof, _ = hp.step(dlayers, profile="time")
+            ev[k][1].record(stream)
+            bfs_ms += prof["bfs_ms"]
+            bfs_launches += prof["bfs_timed_launches"]
+        torch.cuda.synchronize()
+    finally:
+        if clk:
+            clk.__exit__(None, None, None)
+    return {"step_ms": [a.elapsed_time(b) for a, b in ev], "bfs_ms": bfs_ms, "bfs_launches": bfs_launches,
+            "prof_count": prof_count, "accs": accs, "m_and": m_and,
+            "launches": H.homln_kernel_launches() - launches0, "clocks": clk.summary() if clk else None}
+
+
+def roofline(workload, m, hp_tuning):
+    prof = m["prof_count"]
+    alg_bytes_per_launch = bfs_bytes(prof) / max(prof["bfs_launches"], 1)
+    launch_ms = m["bfs_ms"] / max(m["bfs_launches"], 1)
+    achieved = alg_bytes_per_launch / (launch_ms / 1000.0) / 1e9
+    hbm, peak_kind = peaks()
+    traffic = measured_traffic(workload, prof["batches"], prof["words_per_node"], prof["teams"])
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+           "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+           "kernel": "k_msbfs (persistent all-sources BFS: every layer and the AND graph in one launch)",
+           "algorithmic_bytes_per_launch": round(alg_bytes_per_launch), "launch_ms": round(launch_ms, 4),
+           "bfs_share_of_step": round(m["bfs_ms"] / sum(m["step_ms"]), 4)}
+    if traffic:
+        out["dram_gbs"] = round(traffic / (launch_ms / 1000.0) / 1e9, 1)
+        out["dram_frac"] = round(out["dram_gbs"] / hbm, 4)
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import __graft_entry__
@@ -229,57 +372,13 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     net, desc = make_workload(args.workload, rank)
     n, L = net.n, net.n_layers
-    full = (1 << L) - 1
-    work, edge_counts = teps_work(n, net.layers)
-    tuning = {}
-    if args.words:
-        tuning["words_per_node"] = args.words
-    if args.alpha:
-        tuning["push_alpha"] = args.alpha
-    if args.teams:
-        tuning["teams"] = args.teams
-    if args.team_mix:
-        tuning["team_mix"] = 1
-    if args.threads:
-        tuning["threads"] = args.threads
-    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5)
     stream = torch.cuda.current_stream(dev)
+    tuning = tuning_from_args(args)
+    tune_log = None
+    if not tuning and not args.no_autotune and not (args.single_bfs or args.launch_list):
+        tuning, tune_log = autotune_workload(H, net, dev, stream)
+    hp = HotPath(H, net, dev, stream, tuning)
     dlayers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-
-    def step(layers, host_out=False, profile=None):
-        h = H.homln_create(n, layers, stream=stream.cuda_stream)
-        try:
-            if tuning:
-                H.homln_set_tuning(h, **tuning)
-            if profile is not None:
-                H.homln_set_profiling(h, profile == "time", profile == "count")
-            if host_out:
-                F = np.empty(n, np.uint64)
-                R = np.empty(n, np.uint32)
-                cc = np.empty(n, np.float64)
-                ids = [np.empty(n, np.int32) for _ in range(4)]
-            else:
-                F = torch.empty(n, dtype=torch.int64, device=dev)
-                R = torch.empty(n, dtype=torch.int32, device=dev)
-                cc = torch.empty(n, dtype=torch.float64, device=dev)
-                ids = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
-            H.homln_analyse(h, full, True)  # Psi of every layer and the AND graph in one launch
-            outs = []
-            for i in range(L):
-                H.homln_layer_closeness(h, i, F, R, cc)
-                outs.append(None)
-            m_and = H.homln_and_aggregate(h, full)
-            H.homln_and_closeness(h, full, F, R, cc)
-            cg = H.homln_topk(h, -1, full, sel, ids[0])
-            accs = []
-            for j, heur in enumerate((H.HOMLN_NAIVE, H.HOMLN_CC1, H.HOMLN_CC2)):
-                c = H.homln_compose(h, full, heur, sel, ids[j + 1])
-                accs.append(H.homln_accuracy(h, ids[j + 1], c, ids[0], cg))
-            prof = H.homln_get_profile(h) if profile is not None else None
-            return accs, prof, m_and
-        finally:
-            H.homln_destroy(h)
 
     if args.single_bfs:
         h = H.homln_create(n, dlayers, stream=stream.cuda_stream)
@@ -291,63 +390,38 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         return None, net
     if args.launch_list:
-        step(dlayers)
+        hp.step(dlayers)
         torch.cuda.synchronize()
         return None, net
-    # warm-up
-    for _ in range(args.warmup):
-        step(dlayers)
-    torch.cuda.synchronize()
-    # untimed instrumented pass: the algorithmic work of the BFS kernels
-    _, prof_count, m_and = step(dlayers, profile="count")
-    alg_bytes_total = bfs_bytes(prof_count)
-    alg_bytes_per_launch = alg_bytes_total / max(prof_count["bfs_launches"], 1)
-
-    # timed region (device-resident inputs)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = H.homln_kernel_launches()
-    bfs_ms, bfs_launches = 0.0, 0
-    accs = None
-    with ClockSampler(dev.index) as clk:
-        for k in range(args.steps):
-            flush.fill_(k)  # evict L2 between steps (512 MB > 129 MB)
-            ev[k][0].record(stream)
-            accs, prof, _ = step(dlayers, profile="time")
-            ev[k][1].record(stream)
-            bfs_ms += prof["bfs_ms"]
-            bfs_launches += prof["bfs_timed_launches"]
-        torch.cuda.synchronize()
-    launches = H.homln_kernel_launches() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(step_ms) / 1000.0
+    work, edge_counts = teps_work(n, net.layers)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    m = measure(H, hp, dev, args.steps, args.warmup, flush, dist, sample_clocks=True)
+    t_local = sum(m["step_ms"]) / 1000.0
     units, t_max = job_aggregate(work * args.steps, t_local, dist, dev)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
 
-    # end to end through the C-ABI with host buffers: pinned inputs, H2D + D2H inside the timed region
+    # end to end through the C-ABI with host buffers: pinned inputs, H2D + D2H inside the timed region,
+    # over as many steps as the device-timed value
     pinned = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory()) for s, d in net.layers]
     h2d = sum(int(s.numel() + d.numel()) * 4 for s, d in pinned)
     torch.cuda.synchronize()
     e2e_ms = []
-    for k in range(max(1, min(args.steps, 3))):
+    for k in range(args.steps):
         flush.fill_(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step([(s.numpy(), d.numpy()) for s, d in pinned], host_out=True)
+        hp.step([(s.numpy(), d.numpy()) for s, d in pinned], host_out=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
     d2h = (L + 1) * n * (8 + 4 + 8) + 4 * n * 4
-    e2e_t = statistics.mean(e2e_ms) / 1000.0
+    e2e_units, e2e_t = job_aggregate(work * args.steps, sum(e2e_ms) / 1000.0, dist, dev)
 
-    hbm, peak_kind = peaks()
-    achieved = alg_bytes_per_launch / (bfs_ms / max(bfs_launches, 1) / 1000.0) / 1e9
+    prof_count = m["prof_count"]
     result = {
         "metric": METRIC,
-        "value": None,
+        "value": round(units / t_max / 1e9, 3),
         "unit": "GTEPS",
         "n_gpus": world,
         "steps": args.steps,
@@ -361,26 +435,45 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": desc, "n": n, "layers": L, "undirected_edges": edge_counts,
                    "teps_edges_per_step": work, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world} (one HoMLN per GPU)"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4),
-                     "traffic": measured_traffic(args.workload, prof_count["batches"]), "peak_kind": peak_kind,
-                     "kernel": "k_msbfs (persistent all-sources BFS, one launch per graph)",
-                     "algorithmic_bytes_per_launch": round(alg_bytes_per_launch),
-                     "launch_ms": round(bfs_ms / max(bfs_launches, 1), 4),
-                     "bfs_share_of_step": round(bfs_ms / sum(step_ms), 4)},
-        "e2e": {"value": round(work / e2e_t / 1e9, 3), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_t * 1000.0, 3)},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "roofline": roofline(args.workload, m, tuning),
+        "e2e": {"value": round(e2e_units / e2e_t / 1e9, 3), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_t * 1000.0 / args.steps, 3)},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+        "tuning": {"chosen": {"words_per_node": prof_count["words_per_node"], "teams": prof_count["teams"],
+                              "push_alpha": tuning.get("push_alpha", 16)},
+                   "source": "autotuner" if tune_log else ("flags" if tuning else "library defaults"),
+                   "candidates_timed": len(tune_log["candidates"]) if tune_log else 0,
+                   "reps": tune_log["reps"] if tune_log else 0,
+                   "top": tune_log["candidates"][:4] if tune_log else []},
         "accuracy_vs_ground_truth": {nm: {k: round(a[k], 4) for k in ("jaccard", "precision", "recall", "f1")}
-                                     for nm, a in zip(("naive", "cc1", "cc2"), accs)},
+                                     for nm, a in zip(("naive", "cc1", "cc2"), m["accs"])},
         "bfs_profile": {k: prof_count[k] for k in ("levels", "pull_levels", "push_levels", "batches",
                                                    "edges_scanned", "words_gathered", "edges_pushed",
                                                    "words_pushed", "bytes", "visits", "words_per_node",
                                                    "teams")},
     }
-    result["value"] = round(units / t_max / 1e9, 3)
     return result, net
+
+
+def secondary_config(args, name, dev, steps=10, warmup=3):
+    """Another single-GPU configuration measured the same way (device-resident inputs, L2 flushed,
+    CUDA events), autotuned like the headline: GTEPS, ms per step and the BFS kernel's roofline."""
+    import torch
+    from paper_2207_11662_gb300 import homln as H
+    net, desc = make_workload(name, 0)
+    stream = torch.cuda.current_stream(dev)
+    tuning, log = ({}, None) if args.no_autotune else autotune_workload(H, net, dev, stream)
+    hp = HotPath(H, net, dev, stream, tuning)
+    work, _ = teps_work(net.n, net.layers)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    m = measure(H, hp, dev, steps, warmup, flush)
+    t = sum(m["step_ms"]) / 1000.0
+    pc = m["prof_count"]
+    return {"workload": desc, "gteps": round(work * steps / t / 1e9, 3), "ms_per_step": round(t * 1000.0 / steps, 3),
+            "steps": steps, "roofline": roofline(name, m, tuning),
+            "tuning": {"words_per_node": pc["words_per_node"], "teams": pc["teams"],
+                       "push_alpha": tuning.get("push_alpha", 16)}}
 
 
 def batch_vs_plain(args, dev):
@@ -430,7 +523,8 @@ def batch_vs_plain(args, dev):
             best.append(e0.elapsed_time(e1))
         return statistics.mean(best)
 
-    tuning, tune_log = autotune.tune(hs, masks, ns, edges, True, stream.cuda_stream, use_cache=False)
+    skew = max(autotune.degree_skew(net.n, net.layers) for net in nets)
+    tuning, tune_log = autotune.tune(hs, masks, ns, edges, True, stream.cuda_stream, use_cache=False, skew=skew)
     H.homln_set_tuning(hs[0], **tuning)
     timed(lambda: H.homln_batch_analyse(hs, masks, True), reps=1)  # warm-up
     t_batch = timed(lambda: H.homln_batch_analyse(hs, masks, True))
@@ -458,14 +552,15 @@ def batch_vs_plain(args, dev):
             "graph_speedup_vs_plain": round(t_plain / t_graph, 2),
             "speedup_vs_per_homln": round(t_per / t_batch, 2), "batched_gteps": round(work / t_batch / 1e6, 1),
             "identical_outputs": bool(same), "autotuned": tuning,
-            "autotune_candidates_ms": tune_log["candidates"]}
+            "autotune_candidates_timed": len(tune_log["candidates"]), "autotune_reps": tune_log["reps"]}
 
 
 def paper_like(args, dev):
     """Two-layer HoMLNs shaped like the paper's synthetic sets (Section 6, Table 1; seeded R-MAT
     layers over a shared |V|-edge backbone): mean accuracy of naive, CC1 and CC2 against the AND
-    ground truth with above-average CC nodes (Tables 2-5), and the timing comparison of Section 6.1
-    (largest composition time vs smallest layer-analysis time)."""
+    ground truth with above-average CC nodes (Tables 2-5), CC1 at several overlap thresholds theta
+    (Section 5.1 leaves theta undefined), and the timing comparison of Section 6.1 (largest
+    composition time vs smallest layer-analysis time)."""
     import torch
     from paper_2207_11662_gb300 import homln as H
     from paper_2207_11662_gb300 import synth
@@ -473,6 +568,7 @@ def paper_like(args, dev):
     sets = {"S-1": (("powerlaw", "normal"), [(50000, 250000), (100000, 1000000)]),
             "S-2": (("powerlaw", "powerlaw"), [(50000, 250000)]),
             "S-3": (("normal", "normal"), [(50000, 250000)])}
+    thetas = (0.1, 0.25, 0.5)
     sel = H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=0.5)
     names = {"naive": H.HOMLN_NAIVE, "cc1": H.HOMLN_CC1, "cc2": H.HOMLN_CC2}
     out = {}
@@ -480,6 +576,7 @@ def paper_like(args, dev):
     seed = 6001
     for sname, (kinds, bases) in sets.items():
         accs = {k: [] for k in names}
+        sweep = {t: [] for t in thetas}
         for n, m in bases:
             for split in ((0.7, 0.3), (0.6, 0.4), (0.5, 0.5)):
                 seed += 1
@@ -503,13 +600,21 @@ def paper_like(args, dev):
                     c = H.homln_compose(h, 3, heur, sel, est)
                     theta_max[k] = max(theta_max[k], (time.perf_counter() - t0) * 1000.0)
                     accs[k].append(H.homln_accuracy(h, est, c, gt, cg))
+                for t in thetas:
+                    c = H.homln_compose(h, 3, H.HOMLN_CC1, H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=t), est)
+                    sweep[t].append((H.homln_accuracy(h, est, c, gt, cg), c))
                 H.homln_destroy(h)
         out[sname] = {k: {m_: round(100.0 * statistics.mean(a[m_] for a in v), 2)
                           for m_ in ("jaccard", "precision", "recall", "f1")} for k, v in accs.items()}
+        out[sname]["cc1_theta_sweep"] = {
+            str(t): {"jaccard": round(100.0 * statistics.mean(a["jaccard"] for a, _ in v), 2),
+                     "recall": round(100.0 * statistics.mean(a["recall"] for a, _ in v), 2),
+                     "mean_selected": round(statistics.mean(c for _, c in v), 1)} for t, v in sweep.items()}
     out["min_psi_ms"] = round(psi_min, 3)
     out["max_theta_ms"] = {k: round(v, 3) for k, v in theta_max.items()}
     out["max_theta_over_min_psi"] = {k: round(v / psi_min, 3) for k, v in theta_max.items()}
-    out["note"] = ("accuracy in percent (Jaccard is what the paper calls accuracy); paper (Table 2) S-1/S-2/S-3 mean "
+    out["note"] = ("accuracy in percent (Jaccard is what the paper calls accuracy); CC1's overlap threshold theta is "
+                   "not given by the paper (0.5 above, swept in cc1_theta_sweep); paper (Table 2) S-1/S-2/S-3 mean "
                    "Jaccard CC1 43.56/55.95/48.87, CC2 46.77/55.20/50.90 on PaRMAT data, context only")
     return out
 
@@ -612,24 +717,36 @@ def _serving_item(arg):
 def serving(args, dev):
     """Poisson stream (mean 50 req/s) of closeness/top-k queries on HoMLNs of 2-6 layers and
     1,000-100,000 nodes (log-uniform), ER or power-law layers of average degree 6-12, served by the
-    continuous-batching server; latency = completion - arrival."""
+    continuous-batching server; latency = completion - arrival. The server's default (two workers:
+    small requests on a high-priority stream and 32 SMs, big ones on the other SMs, so that their work
+    overlaps on the device) and, on the same stream, one worker whose waves take the whole GPU in
+    arrival order."""
     import multiprocessing as mp
     from paper_2207_11662_gb300 import serve
     from paper_2207_11662_gb300 import synth
     specs = synth.serving_requests(duration_s=args.serve_seconds, rate=args.serve_rate, seed=5001)
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         items = pool.map(_serving_item, [(i, r["spec"], r["t"]) for i, r in enumerate(specs)], chunksize=4)
-    reqs = [serve.Request(i, n, layers, arrival=t, teps_work=w) for i, n, layers, t, w in items]
-    srv = serve.Server(device=dev.index or 0, workers=1, max_wave=16, mem_budget_bytes=32 << 30)
-    t0 = time.perf_counter()
-    done = srv.run(reqs, realtime=True)
-    wall = time.perf_counter() - t0
-    out = serve.latency_stats(done, wall)
-    out.update({"duration_s": round(wall, 2), "rate_req_per_s": args.serve_rate, "workers": 1, "max_wave": 16,
-                "waves": srv.waves, "errors": srv.errors[:3],
+
+    def run(**kw):
+        reqs = [serve.Request(i, n, layers, arrival=t, teps_work=w) for i, n, layers, t, w in items]
+        srv = serve.Server(device=dev.index or 0, max_wave=16, mem_budget_bytes=32 << 30, **kw)
+        t0 = time.perf_counter()
+        done = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        out = serve.latency_stats(done, wall, srv.big_work)
+        out.update({"duration_s": round(wall, 2), "workers": srv.workers, "waves": srv.waves,
+                    "errors": srv.errors[:3]})
+        if srv.workers >= 2:
+            out["small_sms"] = srv.small_sms
+        return out
+
+    out = run()
+    out["one_worker_whole_gpu"] = run(workers=1)
+    out.update({"rate_req_per_s": args.serve_rate, "max_wave": 16,
                 "workload": "Poisson arrivals, HoMLNs of 2-6 layers, n log-uniform in [1e3, 1e5], ER or "
                             "Chung-Lu layers (avg deg 6-12); per request: Psi of all layers + AND, top-10% ground "
-                            "truth, CC2 estimate and its accuracy"})
+                            "truth, CC2 estimate and its accuracy; big = nodes x edges > 2e10"})
     return out
 
 
@@ -671,6 +788,32 @@ def cpu_baseline(net, sources_per_graph: int, seed: int = 2001, one_core_sources
     return out
 
 
+def summary(result: dict) -> dict:
+    """The few figures a reader wants first, kept at the end of the line."""
+    r = result.get("roofline", {})
+    out = {"headline": f"{result['value']} GTEPS, {result['ms_per_step']} ms/step (200k BA)"
+                       if "200000" in result["config"]["workload"] else f"{result['value']} GTEPS",
+           "bfs_alg_frac": r.get("frac"), "bfs_dram_frac": r.get("dram_frac"),
+           "e2e_gteps": result["e2e"]["value"]}
+    for name, c in result.get("configs", {}).items():
+        out[f"{name}_gteps"] = c["gteps"]
+        out[f"{name}_bfs_alg_frac"] = c["roofline"]["frac"]
+    b = result.get("batched_vs_plain")
+    if b:
+        out["batched"] = {"batched_ms": b["batched_ms"], "graph_replay_ms": b["graph_replay_ms"],
+                          "plain_ms": b["plain_ms"], "speedup_vs_plain": b["speedup_vs_plain"],
+                          "graph_speedup_vs_plain": b["graph_speedup_vs_plain"],
+                          "identical_outputs": b["identical_outputs"]}
+    v = result.get("serving")
+    if v:
+        out["serving"] = {k: v[k] for k in ("p50_ms", "p90_ms", "p99_ms", "req_per_s") if k in v}
+        out["serving"]["small_p99_ms"] = v["small"]["p99_ms"]
+        one = v.get("one_worker_whole_gpu")
+        if one:
+            out["serving"]["one_worker"] = {k: one[k] for k in ("p50_ms", "p90_ms", "p99_ms")}
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -707,17 +850,26 @@ def main():
     if rank == 0:
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        extra = {}
+        if args.secondary != "none" and args.secondary != args.workload and world == 1:
+            extra["configs"] = {args.secondary: secondary_config(args, args.secondary, dev)}
         if not args.no_batch and world == 1:
-            result["batched_vs_plain"] = batch_vs_plain(args, dev)
+            extra["batched_vs_plain"] = batch_vs_plain(args, dev)
         if not args.no_serve and world == 1:
-            result["serving"] = serving(args, dev)
+            extra["serving"] = serving(args, dev)
         if not args.no_paper_like and world == 1:
-            result["paper_like"] = paper_like(args, dev)
+            extra["paper_like"] = paper_like(args, dev)
         if not args.no_widened and world == 1:
-            result["widened"] = widened(args, dev)
+            extra["widened"] = widened(args, dev)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources, one_core_sources=150)
-        print(json.dumps(result))
+        # headline keys first, the long detail next, the summary last
+        head = {k: result.pop(k) for k in list(result) if k not in ("accuracy_vs_ground_truth", "bfs_profile")}
+        out = dict(head)
+        out.update(result)
+        out.update(extra)
+        out["summary"] = summary(out)
+        print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
 
