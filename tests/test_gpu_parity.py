@@ -546,101 +546,6 @@ def test_allocator_failure_and_torch_allocator(H):
     g.close()
 
 
-def test_powerlaw_full_size_sampled(H):
-    """4 Chung-Lu layers on 50,000 nodes (the benchmark workload), in the benchmark's launch configuration;
-    F and R checked at a seeded 2,000-vertex sample by oracle BFS from those vertices, the rest by properties."""
-    import torch
-    net = synth.homln_powerlaw()
-    n, L = net.n, net.n_layers
-    g = H.Network(n, to_dev(net.layers))
-    rng = np.random.default_rng(2001)
-    sample = np.sort(rng.choice(n, 2000, replace=False)).astype(np.int32)
-    keys = [O.edge_keys(n, s, d) for s, d in net.layers]
-    graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
-    outs = [g.layer_closeness(i) for i in range(L)] + [g.and_closeness((1 << L) - 1)]
-    for (rp, col), (F, R, cc) in zip(graphs, outs):
-        Fs, Rs = O.farness_reach(n, rp, col, sources=sample, threads=8)
-        assert np.array_equal(u64(F)[sample], Fs)
-        assert np.array_equal(R.cpu().numpy().astype(np.uint32)[sample], Rs)
-        assert np.array_equal(cc.cpu().numpy()[sample], O.wf_closeness(n, Fs, Rs))
-        # properties at every vertex: sum over v of F equals sum over v of R-weighted distances is symmetric;
-        # R is |component| - 1, so vertices of one component share R; F >= R
-        Fa, Ra = u64(F), R.cpu().numpy().astype(np.uint64)
-        assert np.all(Fa >= Ra)
-        assert np.all((Ra == 0) == (Fa == 0))
-    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0)
-    k = O.topk_count(O.Select(), n)
-    for which in list(range(L)) + [-1]:
-        top = g.topk(which, (1 << L) - 1, sel).cpu().numpy()
-        cc = (outs[which][2] if which >= 0 else outs[-1][2]).cpu().numpy()
-        assert top.shape[0] == k and len(set(top.tolist())) == k
-        # ranking property: scores non-increasing, ties by ascending id, nothing outside beats the last one
-        s = cc[top]
-        assert np.all(s[:-1] >= s[1:])
-        tie = s[:-1] == s[1:]
-        assert np.all(top[:-1][tie] < top[1:][tie])
-        rest = np.setdiff1d(np.arange(n), top)
-        assert np.all((cc[rest] < s[-1]) | ((cc[rest] == s[-1]) & (rest > top[-1])))
-    naive = g.compose((1 << L) - 1, H.HOMLN_NAIVE, sel).cpu().numpy()
-    cc1 = g.compose((1 << L) - 1, H.HOMLN_CC1, sel).cpu().numpy()
-    cc2 = g.compose((1 << L) - 1, H.HOMLN_CC2, sel).cpu().numpy()
-    assert set(cc1.tolist()) <= set(naive.tolist())
-    for i in range(L):
-        assert set(naive.tolist()) <= set(g.topk(i, 1, sel).cpu().numpy().tolist())
-    assert cc2.shape[0] == k and np.all(np.diff(cc2) > 0)
-    g.close()
-    torch.cuda.synchronize()
-
-
-def sampled_check(n, rowptr, col, F, R, cc, sample):
-    Fs, Rs = O.farness_reach(n, rowptr, col, sources=sample, threads=8)
-    assert np.array_equal(u64(F)[sample], Fs)
-    assert np.array_equal(R.cpu().numpy().astype(np.uint32)[sample], Rs)
-    assert np.array_equal(cc.cpu().numpy()[sample], O.wf_closeness(n, Fs, Rs))
-
-
-def test_batch_config_full_size_sampled(H):
-    """The batched workload at full size (64 HoMLNs, 2-8 layers, 500-20,000 nodes, ER/BA layers) in one
-    persistent launch with several teams; F/R/closeness at 64 seeded vertices of every graph."""
-    nets = synth.homln_batch(64, 3001)
-    gs = [H.Network(net.n, to_dev(net.layers)) for net in nets]
-    H.homln_set_tuning(gs[0].h, teams=16)
-    masks = [(1 << net.n_layers) - 1 for net in nets]
-    H.homln_batch_analyse([g.h for g in gs], masks, True)
-    rng = np.random.default_rng(3001)
-    for g, net, mask in zip(gs, nets, masks):
-        keys = [O.edge_keys(net.n, s, d) for s, d in net.layers]
-        graphs = [O.csr_from_keys(net.n, k) for k in keys] + [O.csr_from_keys(net.n, O.and_keys(net.n, keys))]
-        outs = [g.layer_closeness(i) for i in range(net.n_layers)] + [g.and_closeness(mask)]
-        sample = np.sort(rng.choice(net.n, 64, replace=False)).astype(np.int32)
-        for (rp, col), (F, R, cc) in zip(graphs, outs):
-            sampled_check(net.n, rp, col, F, R, cc, sample)
-        g.close()
-
-
-def test_large_ba_full_size_sampled(H):
-    """4 Barabasi-Albert layers on 200,000 nodes with ~50% shared edges: F/R/closeness at 300 seeded
-    vertices per graph; CC2 on the full graph checked by its ranking properties."""
-    net = synth.homln_ba_large()
-    n, L = net.n, net.n_layers
-    g = H.Network(n, to_dev(net.layers))
-    g.analyse((1 << L) - 1, True)
-    keys = [O.edge_keys(n, s, d) for s, d in net.layers]
-    graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
-    outs = [g.layer_closeness(i) for i in range(L)] + [g.and_closeness((1 << L) - 1)]
-    sample = np.sort(np.random.default_rng(4001).choice(n, 300, replace=False)).astype(np.int32)
-    for (rp, col), (F, R, cc) in zip(graphs, outs):
-        sampled_check(n, rp, col, F, R, cc, sample)
-    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0)
-    k = O.topk_count(O.Select(), n)
-    cc2 = g.compose((1 << L) - 1, H.HOMLN_CC2, sel).cpu().numpy()
-    naive = g.compose((1 << L) - 1, H.HOMLN_NAIVE, sel).cpu().numpy()
-    assert cc2.shape[0] == k and np.all(np.diff(cc2) > 0)
-    for i in range(L):
-        assert set(naive.tolist()) <= set(g.topk(i, 1, sel).cpu().numpy().tolist())
-    g.close()
-
-
 def test_bounded_wait_runs_out_and_the_handle_recovers(H):
     """Failure detection: team barriers that wait for blocks that do not exist give up after the
     wait limit; the call reports HOMLN_ETIMEOUT, the handle drops its results and stays usable."""
