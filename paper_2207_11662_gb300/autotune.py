@@ -24,7 +24,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 WORDS = (4, 8, 16, 32)           # 256 .. 2048 sources per tile
 TEAMS = (0, 4, 8, 16, 32, 76, 152)  # 0: the library's default for the chosen W
 ALPHAS = (4, 16, 64)             # top-down while alpha * frontier edges < unfinished edges
-STATE_LIMIT = 2.0e9              # bytes of BFS state a candidate may take (3 arrays of n x W words per team)
+STATE_LIMIT = 2.0e9              # bytes of BFS state a candidate may take (2 snapshots of n x W words per team)
 
 
 def workload_key(ns, edges, skew: float = 1.0) -> str:
@@ -108,10 +108,10 @@ def tune(handles, masks, ns, edges, with_and=True, stream_ptr: int = 0, use_cach
         return seen[k]
 
     # W: no wider than the node count needs, one team's state within the limit
-    ws = [w for w in words if 64 * (w // 2) < maxn and 3.0 * maxn * 8.0 * w <= STATE_LIMIT] or [1]
+    ws = [w for w in words if 64 * (w // 2) < maxn and 2.0 * maxn * 8.0 * w <= STATE_LIMIT] or [1]
     best = min(({"words_per_node": w, "teams": 0, "push_alpha": 16} for w in ws), key=run)
     tiles = sum(-(-n // (64 * best["words_per_node"])) for n in ns)
-    per_team = 3.0 * maxn * 8.0 * best["words_per_node"]
+    per_team = 2.0 * maxn * 8.0 * best["words_per_node"]
     tcands = [t for t in teams if t == 0 or (t <= tiles and t * per_team <= STATE_LIMIT)]
     best = min((dict(best, teams=t) for t in tcands), key=run)
     best = min((dict(best, push_alpha=a) for a in alphas), key=run)

@@ -8,12 +8,13 @@
 //     R[v] = number of those vertices, v excluded.
 //
 // How: sources are processed in batches of S = 64*W. Every vertex carries S-bit
-// words -- seen and two frontier buffers -- one bit per source of the batch. A
+// words, one bit per source of the batch, in two snapshots: after level l,
+// snapshot l mod 2 holds for every vertex the sources within distance l. A
 // level either pulls (bottom-up: the new bits of v are the OR of its
-// (in-)neighbours' frontier words, minus seen[v]) or pushes (top-down: every
-// vertex with new bits on the previous level ORs its words into its
-// (out-)neighbours' next frontier words, then a sweep keeps the bits not yet
-// seen). A bit of source s that first reaches v at level l means d(s, v) = l,
+// (in-)neighbours' words in the previous snapshot, minus v's own) or pushes
+// (top-down: every vertex with new bits on the previous level ORs its words into
+// its (out-)neighbours' words of the next snapshot, then a sweep keeps the bits
+// they did not have). A bit of source s that first reaches v at level l means d(s, v) = l,
 // which undirected is d(v, s): F[v] += l * popc(new[v]), R[v] += popc(new[v]),
 // with no per-source scatter; directed, the same sum is v's in-farness.
 //
@@ -57,7 +58,7 @@ struct TeamArgs {
     int32_t nteams;
     int32_t push_alpha;
     int64_t maxn;               // per-team state stride in vertices
-    uint64_t *state;            // [3 arrays][nteams][maxn * W]: seen, frontier A, frontier B
+    uint64_t *state;            // [2 snapshots][nteams][maxn * W]
     uint8_t *quiet;             // [nteams][maxn]
     uint8_t *fresh;             // [nteams][maxn]
     uint8_t *pushed;            // [nteams][maxn]
@@ -92,7 +93,6 @@ struct Tile {
     const int32_t *__restrict__ col;
     const int64_t *__restrict__ prow;    // in-edges (pull)
     const int32_t *__restrict__ pcol;
-    uint64_t *seen;
     uint8_t *quiet;
     uint8_t *fresh;
     uint8_t *pushed;  // a top-down level ORed words into the vertex's next frontier words
@@ -110,14 +110,14 @@ struct Tile {
     bool atomic_fr;
 };
 
-// Frontier words are written only by the lanes of a vertex that found new bits; otherwise
-// they keep bits the vertex found at an earlier level of the same batch. Such stale bits
-// never add a bit: a reader w (a neighbour, or an out-neighbour when directed) of v already
-// has each of them, since a source found at v on level l reaches w by level l + 1, before w
-// reads that buffer again at level l + 2. Both frontier buffers start a batch at zero.
-// A vertex is "quiet" once its seen word is full: every later level of the batch skips it
-// after reading one byte. fresh[v] marks the last level at which v found new bits, so that a
-// top-down level pushes only the words written on the level before.
+// Two snapshots per team: level l reads snapshot (l-1) mod 2 and writes snapshot l mod 2.
+// Invariant: after level l, snapshot l mod 2 holds state_l(v) -- the sources within distance
+// l of v -- for every vertex. A vertex rewrites its words of the next snapshot only if it
+// finds new bits at level l, or found some at level l-1 (then the next snapshot still holds
+// state_{l-2}, which differs); otherwise they already hold state_{l-2} = state_{l-1} =
+// state_l. fresh[v] marks the last level at which v found new bits. A vertex is "quiet" once
+// both snapshots hold every bit (one level after its words became full): every later level
+// of the batch skips it after reading one byte, and nobody pushes to it.
 constexpr uint8_t QUIET = 1;  // quiet byte of a full vertex
 
 __device__ __forceinline__ uint8_t level_mark(int level) { return (uint8_t)(1 + level % 255); }
@@ -408,14 +408,16 @@ __device__ __forceinline__ void reset_next_slot(const Tile &a, uint32_t ps) {
     }
 }
 
-// Record the new bits of v (already reduced to this lane's K words) and its counters.
+// Record the new bits nw of v (this lane's K words; s = its words in the previous snapshot)
+// in the next snapshot nxt, and its counters. changed_last: v found new bits on the previous
+// level, so its words in nxt are out of date and are rewritten even without new bits.
 template <int W, bool STATS>
 __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writer, int64_t v, int q,
                                               const uint64_t (&s)[Geo<W>::K], const uint64_t (&nw)[Geo<W>::K],
-                                              uint64_t *nxt, int level, int64_t deg,
+                                              uint64_t *nxt, int level, int64_t deg, bool changed_last,
                                               PhaseCounters &c, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
-    bool any = false, full = true;
+    bool any = false, full = true, sfull = true;
     uint32_t cnt = 0;
     uint64_t ns[K];
 #pragma unroll
@@ -423,15 +425,16 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
         ns[k] = s[k] | nw[k];
         any |= nw[k] != 0;
         full &= ns[k] == ~0ull;
+        sfull &= s[k] == ~0ull;
         cnt += __popcll(nw[k]);
     }
-    if (act && writer && any) {
-        stw<K>(a.seen + v * W + q * K, ns);
-        stw<K>(nxt + v * W + q * K, nw);
-        if (STATS) st[ST_BYTES] += 16 * K;
+    if (act && writer && (any || changed_last)) {
+        stw<K>(nxt + v * W + q * K, ns);
+        if (STATS) st[ST_BYTES] += 8 * K;
     }
     cnt = group_sum<T>(cnt);
     const bool gfull = !group_any<T>(!full);
+    const bool gsfull = !group_any<T>(!sfull);
     if (act && writer && q == 0) {
         if (cnt) {
             if (a.atomic_fr) {
@@ -447,21 +450,23 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
             if (STATS) st[ST_BYTES] += 25;
         }
         if (!gfull) c.mu += (unsigned long long)deg;
-        if (gfull) a.quiet[v] = QUIET;
+        // full in the previous snapshot: the next one is full now too (rewritten above, as a vertex
+        // becomes full on the level after its last new bits)
+        if (gsfull) a.quiet[v] = QUIET;
         if (STATS) st[ST_VISITS] += 1;
     }
 }
 
 // ---------------------------------------------------------------- phases
 
-// Level 0 of a batch: seen = the bits of the sources that cannot reach the vertex (the padding
-// bits of a short last batch; the batch's sources on the other side of the split at gend) and
-// its own source bit; both frontier buffers 0; the per-vertex bytes 0, except that a vertex that
+// Level 0 of a batch: both snapshots = the bits of the sources that cannot reach the vertex (the
+// padding bits of a short last batch; the batch's sources on the other side of the split at gend)
+// and its own source bit; the per-vertex bytes 0, except that a vertex that
 // no other source of the batch can reach (none on its side of the split, or no in-edges) is
-// quiet from the start. The unreachable bits never arrive, so without them in `seen` no vertex
+// quiet from the start. The unreachable bits never arrive, so without them no vertex
 // of a batch that mixes the two sides would ever become full.
 template <int W, bool STATS>
-__device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int32_t s0, int32_t ns,
+__device__ void phase_start_batch(const Tile &a, uint64_t *s0buf, uint64_t *s1buf, int32_t s0, int32_t ns,
                                   unsigned long long *st) {
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
@@ -481,21 +486,20 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *fa, uint64_t *fb, int
             const int b = (int)(v - s0);
             if ((b >> 6) == wi) x |= 1ull << (b & 63);
         }
-        a.seen[i] = x;
-        fa[i] = 0;
-        fb[i] = 0;
+        s0buf[i] = x;  // both snapshots hold state_0
+        s1buf[i] = x;
         if (wi == 0) {
             const bool lonely = c1 - c0 - (source ? 1 : 0) <= 0 || a.prow[v + 1] == a.prow[v];
             a.quiet[v] = lonely ? QUIET : 0;
             a.fresh[v] = 0;
             a.pushed[v] = 0;
         }
-        if (STATS) st[ST_BYTES] += 24 + (wi == 0 ? 3 + 16 : 0);
+        if (STATS) st[ST_BYTES] += 16 + (wi == 0 ? 3 + 16 : 0);
     }
 }
 
-// Level 1, top-down: every source ORs its bit into its neighbours' words of the first frontier
-// buffer (zeroed by phase_start_batch before a team barrier).
+// Level 1, top-down: every source ORs its bit into its neighbours' words of snapshot 1 (which
+// holds state_0, written by phase_start_batch before a team barrier).
 template <int W, bool STATS>
 __device__ void phase_start_push(const Tile &a, uint64_t *fa, int32_t s0, int32_t ns, unsigned long long *st) {
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
@@ -515,24 +519,27 @@ __device__ void phase_start_push(const Tile &a, uint64_t *fa, int32_t s0, int32_
     }
 }
 
-// After a top-down level: of the words pushed into a vertex's next frontier words, the bits not
-// yet seen are its new bits (the rest, and what the words held before, are bits it has).
+// After a top-down level: of the words pushed into a vertex's words of the next snapshot (which
+// held state_{l-2}), the bits it did not have after the previous level are its new bits.
 template <int W, bool STATS>
-__device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t ps, PhaseCounters &c,
-                               unsigned long long *st) {
+__device__ void phase_finalize(const Tile &a, const uint64_t *__restrict__ prv, uint64_t *nxt, int level, uint32_t ps,
+                               PhaseCounters &c, unsigned long long *st) {
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     reset_next_slot(a, ps);
     const int lane = threadIdx.x & 31, q = lane % T;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
+    const uint8_t last = level_mark(level - 1);
     for (int64_t v = gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-        uint8_t qv = 0, pv = 0;
+        uint8_t qv = 0, pv = 0, fv = 0;
         if (v < a.n) {
             qv = a.quiet[v];
             pv = a.pushed[v];
-            if (STATS && q == 0) st[ST_BYTES] += 2;
+            fv = a.fresh[v];
+            if (STATS && q == 0) st[ST_BYTES] += 3;
         }
         const bool act = v < a.n && qv < QUIET;
+        const bool chg = fv == last;
         uint64_t s[K], nw[K];
         int64_t deg = 0;
 #pragma unroll
@@ -540,17 +547,21 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
         if (act) {
             deg = a.rowptr[v + 1] - a.rowptr[v];
             if (STATS && q == 0) st[ST_BYTES] += 16;
-            // a vertex nobody pushed to has no new bits (and, not being quiet, is not full)
+            // a vertex nobody pushed to has no new bits; its next words are current unless it
+            // found bits on the previous level (a non-quiet vertex whose words are full did)
+            if (pv || chg) {
+                ldw<K>(prv + v * W + q * K, s);
+                if (STATS) st[ST_BYTES] += 8 * K;
+            }
             if (pv) {
                 uint64_t z[K];
                 ldw<K>(nxt + v * W + q * K, z);
-                ldw<K>(a.seen + v * W + q * K, s);
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
-                if (STATS) st[ST_BYTES] += 16 * K;
+                if (STATS) st[ST_BYTES] += 8 * K;
             }
         }
-        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, c, st);
+        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, act && chg, c, st);
         // after the group's shuffles in commit_vertex: every lane of the group has read pv
         if (act && pv && q == 0) a.pushed[v] = 0;
     }
@@ -561,8 +572,10 @@ __device__ void phase_finalize(const Tile &a, uint64_t *nxt, int level, uint32_t
 template <int W, bool STATS>
 __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint64_t *nxt, int level, uint32_t ps,
                            PhaseCounters &c, unsigned long long *st) {
+    // cur: the previous snapshot (read: the vertex's own words and its neighbours'); nxt: the next
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     reset_next_slot(a, ps);
+    const uint8_t last = level_mark(level - 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = lane % T;
 
@@ -574,8 +587,9 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             const uint8_t qv = a.quiet[v];
             if (STATS && threadIdx.x == 0) st[ST_BYTES] += 1;
             if (qv >= QUIET) continue;  // uniform over the block
+            const bool chg = a.fresh[v] == last;  // read by every thread before warp 0 commits
             uint64_t s[K], need[K], acc[K];
-            ldw<K>(a.seen + v * W + q * K, s);
+            ldw<K>(cur + v * W + q * K, s);
             bool lane_need = false;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -615,7 +629,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                         for (int k = 0; k < K; ++k) t[k] |= red[w][lane][k];
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = t[k] & need[k];
-                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, c, st);
+                commit_vertex<W, STATS>(a, true, lane < T, v, q, s, nw, nxt, level, re - rb, chg, c, st);
             }
             __syncthreads();
         }
@@ -632,8 +646,9 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             const uint8_t qv = a.quiet[v];
             if (STATS && lane == 0) st[ST_BYTES] += 1;
             if (qv >= QUIET) continue;  // uniform over the warp
+            const bool chg = a.fresh[v] == last;
             uint64_t s[K], need[K], acc[K], nw[K];
-            ldw<K>(a.seen + v * W + q * K, s);
+            ldw<K>(cur + v * W + q * K, s);
             bool lane_need = false;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -666,7 +681,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 for (int k = 0; k < K; ++k) acc[k] |= __shfl_xor_sync(0xffffffffu, acc[k], o);
 #pragma unroll
             for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, c, st);
+            commit_vertex<W, STATS>(a, true, p == 0, v, q, s, nw, nxt, level, re - rb, chg, c, st);
         }
     }
     // --- group tier: T lanes per vertex. Warps take chunks of consecutive vertices from the
@@ -691,14 +706,17 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             // lane i holds vertex v0+i's row bounds and quiet byte (i < cnt)
             const int64_t rb_l = a.prow[v0 + min(lane, cnt)];
             const int64_t re_l = a.prow[v0 + min(lane + 1, cnt)];
-            const int q_l = lane < cnt ? (int)a.quiet[v0 + lane] : (int)QUIET;
+            // quiet byte | fresh byte << 8 of vertex v0+lane
+            const int qf_l = lane < cnt ? (int)a.quiet[v0 + lane] | ((int)a.fresh[v0 + lane] << 8) : (int)QUIET;
             for (int pass = 0; pass * per_pass < cnt; ++pass) {  // uniform over the warp
                 const int i = pass * per_pass + lane / T;
                 const int64_t v = v0 + i;
-                const int qv = __shfl_sync(0xffffffffu, q_l, i & 31);
+                const int qf = __shfl_sync(0xffffffffu, qf_l, i & 31);
+                const int qv = qf & 0xff;
+                const bool chg = (qf >> 8) == (int)last;
                 const int64_t rb0 = __shfl_sync(0xffffffffu, (long long)rb_l, i & 31);
                 const int64_t re0 = __shfl_sync(0xffffffffu, (long long)re_l, i & 31);
-                if (STATS && q == 0 && i < cnt) st[ST_BYTES] += 1;
+                if (STATS && q == 0 && i < cnt) st[ST_BYTES] += 2;
                 const bool act = i < cnt && qv < QUIET;
                 uint64_t s[K], need[K], acc[K], nw[K];
                 int32_t u[kUnroll];
@@ -709,7 +727,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 if (act) {
                     rb = rb0;
                     re = re0;
-                    ldw<K>(a.seen + v * W + q * K, s);
+                    ldw<K>(cur + v * W + q * K, s);
                     load_cols(a, rb, re, 1, u);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
@@ -728,15 +746,16 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 }
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, c, st);
+                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, act && chg, c, st);
             }
         }
     }
     flush_counters(a, c, ps);
 }
 
-// Top-down level: frontier vertices OR their words into the neighbours' accumulators
-// (quiet neighbours are full and are skipped).
+// Top-down level: the vertices with new bits on the previous level OR their words of the previous
+// snapshot into their neighbours' words of the next snapshot (quiet neighbours are full and are
+// skipped). The whole words are pushed: bits a neighbour already has are masked by the sweep.
 template <int W, bool STATS>
 __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint64_t *nxt, int level, uint32_t ps,
                            unsigned long long *st) {
@@ -789,16 +808,16 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint
 // The levels of one batch (sources s0 .. s0+ns-1) of one graph, run by one team.
 // Returns false if a barrier gave up (the kernel must stop).
 template <int W, bool STATS>
-__device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamBarrier &tb, int32_t s0, int32_t ns,
+__device__ bool run_batch(const Tile &a, uint64_t *sa, uint64_t *sb, const TeamBarrier &tb, int32_t s0, int32_t ns,
                           uint32_t &ps, PhaseCounters &c, unsigned long long *st) {
-    phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st);
+    phase_start_batch<W, STATS>(a, sa, sb, s0, ns, st);
     if (!team_sync(tb)) return false;
-    phase_start_push<W, STATS>(a, fa, s0, ns, st);
+    phase_start_push<W, STATS>(a, sb, s0, ns, st);
     if (!team_sync(tb)) return false;
-    phase_finalize<W, STATS>(a, fa, 1, ps, c, st);
+    phase_finalize<W, STATS>(a, sa, sb, 1, ps, c, st);
     ++ps;
     if (!team_sync(tb)) return false;
-    uint64_t *cur = fa, *nxt = fb;
+    uint64_t *cur = sb, *nxt = sa;  // level l reads snapshot (l-1) mod 2, writes l mod 2
     if (STATS) { st[ST_BATCHES] += 1; st[ST_LEVELS] += 1; st[ST_PUSH] += 1; }
     for (int level = 2; level <= a.n + 1; ++level) {
         const unsigned long long *slot = a.ctr + 4 * ((ps - 1) % 3);
@@ -808,7 +827,7 @@ __device__ bool run_batch(const Tile &a, uint64_t *fa, uint64_t *fb, const TeamB
         if (push) {
             phase_push<W, STATS>(a, cur, nxt, level, ps, st);
             if (!team_sync(tb)) return false;
-            phase_finalize<W, STATS>(a, nxt, level, ps, c, st);
+            phase_finalize<W, STATS>(a, cur, nxt, level, ps, c, st);
         } else {
             phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st);
         }
@@ -856,9 +875,8 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     const TeamBarrier tb{tbar, tbar + 1, A.err, (uint32_t)(tsize + A.phantom), A.wait_ns};
     const size_t stride = (size_t)A.maxn * W;
     const size_t arr = stride * A.nteams;
-    uint64_t *seen = A.state + 0 * arr + team * stride;
-    uint64_t *fa = A.state + 1 * arr + team * stride;
-    uint64_t *fb = A.state + 2 * arr + team * stride;
+    uint64_t *sa = A.state + 0 * arr + team * stride;  // snapshot 0
+    uint64_t *sb = A.state + 1 * arr + team * stride;  // snapshot 1
     uint8_t *quiet = A.quiet + (size_t)team * A.maxn;
     uint8_t *fresh = A.fresh + (size_t)team * A.maxn;
     uint8_t *pushed = A.pushed + (size_t)team * A.maxn;
@@ -882,7 +900,6 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
         a.col = g.col;
         a.prow = g.prow;
         a.pcol = g.pcol;
-        a.seen = seen;
         a.quiet = quiet;
         a.fresh = fresh;
         a.pushed = pushed;
@@ -907,7 +924,7 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
         const int32_t b = g.b0 + (t - g.tile0) * g.bstride;
         const int32_t s0 = b * 64 * W;
         const int32_t ns = min(64 * W, g.n - s0);
-        ok = run_batch<W, STATS>(a, fa, fb, tb, s0, ns, ps, c, st);
+        ok = run_batch<W, STATS>(a, sa, sb, tb, s0, ns, ps, c, st);
     }
     if (STATS && A.stats) {
         if (threadIdx.x == 0 && rank == 0) {
@@ -938,13 +955,12 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     for (int i = 0; i < ST_N; ++i) st[i] = 0;
     const GraphDesc &g = A.graphs[gi];
     const size_t arr = (size_t)A.maxn * W;
-    uint64_t *fa = A.state + 1 * arr, *fb = A.state + 2 * arr;
+    uint64_t *sa = A.state, *sb = A.state + arr;
     Tile a;
     a.rowptr = g.rowptr;
     a.col = g.col;
     a.prow = g.prow;
     a.pcol = g.pcol;
-    a.seen = A.state;
     a.quiet = A.quiet;
     a.fresh = A.fresh;
     a.pushed = A.pushed;
@@ -963,11 +979,12 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     a.tsize = gridDim.x;
     a.push_alpha = A.push_alpha;
     a.atomic_fr = false;
-    uint64_t *cur = cur_is_a ? fa : fb, *nxt = cur_is_a ? fb : fa;
+    // level 1 (cur_is_a = 0) reads snapshot 0 and writes snapshot 1; the host alternates after
+    uint64_t *cur = cur_is_a ? sb : sa, *nxt = cur_is_a ? sa : sb;
     switch (kind) {
-    case PH_START: phase_start_batch<W, STATS>(a, fa, fb, s0, ns, st); break;
-    case PH_START_PUSH: phase_start_push<W, STATS>(a, fa, s0, ns, st); break;
-    case PH_FINALIZE: phase_finalize<W, STATS>(a, nxt, level, ps, c, st); break;
+    case PH_START: phase_start_batch<W, STATS>(a, sa, sb, s0, ns, st); break;
+    case PH_START_PUSH: phase_start_push<W, STATS>(a, sb, s0, ns, st); break;
+    case PH_FINALIZE: phase_finalize<W, STATS>(a, cur, nxt, level, ps, c, st); break;
     case PH_PULL: phase_pull<W, STATS>(a, cur, nxt, level, ps, c, st); break;
     default: phase_push<W, STATS>(a, cur, nxt, level, ps, st); break;
     }
@@ -1034,7 +1051,7 @@ BfsKernel kernel_for(int W, bool stats) {
     }
 }
 
-// Widest tile: one team's state (3 arrays of n x W words) stays within this many bytes.
+// Widest tile: one team's state (2 snapshots of n x W words) stays within this many bytes.
 constexpr double kWordsBudget = 104.0e6;
 // Default teams: as many as keep the state of all teams near kTeamState bytes (about twice
 // L2), at least kDefaultTeams, and never more state than kStateCap bytes. Measured on GB300
@@ -1050,7 +1067,7 @@ constexpr double kStateCap = 2.0e9;
 
 int msbfs_pick_words(int32_t n) {
     int W = 32;
-    while (W > 1 && 3.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
+    while (W > 1 && 2.0 * n * 8.0 * W > kWordsBudget) W >>= 1;
     while (W > 1 && (int64_t)64 * (W / 2) >= n) W >>= 1;  // no wider than the node count needs
     return W;
 }
@@ -1105,7 +1122,7 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
         if (t.teams > 0) {
             nteams = t.teams;
         } else {
-            const double per_team = 3.0 * maxn * 8.0 * W;  // bytes of one team's state
+            const double per_team = 2.0 * maxn * 8.0 * W;  // bytes of one team's state
             nteams = std::max(kDefaultTeams, (int)std::floor(kTeamState / per_team));
             nteams = std::max(1, std::min(nteams, (int)std::floor(kStateCap / per_team)));
             int64_t tiles = 0;  // no more teams than tiles
@@ -1169,7 +1186,7 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
 
     const size_t words = (size_t)maxn * W * nteams;
     p->bar_words = 32 * (size_t)nteams + 32 + (size_t)nsm;  // team barriers, grid barrier, SM slots
-    if (!p->state.alloc(al, 3 * words) || !p->quiet.alloc(al, 3 * (size_t)maxn * nteams) ||
+    if (!p->state.alloc(al, 2 * words) || !p->quiet.alloc(al, 3 * (size_t)maxn * nteams) ||
         !p->ctr.alloc(al, 16 * nteams) || !p->barmem.alloc(al, p->bar_words) || !p->queue.alloc(al, 1) ||
         !p->d_desc.alloc(al, ng))
         fail(HOMLN_ENOMEM, "bfs state");

@@ -63,7 +63,7 @@ class Request:
 def footprint_bytes(n: int, edge_counts) -> int:
     """Estimated peak device bytes of one request: the layer CSRs and their relabelled copies,
     the AND graph, the construction scratch, the per-graph outputs and the BFS state (per team
-    3 arrays of n x 8 words and 3 bytes per node; the library's default team count: at least
+    2 snapshots of n x 8 words and 3 bytes per node; the library's default team count: at least
     16, up to about 240 MB of state in all, and no more teams than tiles of 512 sources)."""
     m = int(sum(edge_counts))
     L = len(edge_counts)
@@ -71,8 +71,8 @@ def footprint_bytes(n: int, edge_counts) -> int:
     build = 8 * 2 * max(edge_counts, default=0) * 3  # sort keys, alternate keys, flags of one layer
     outputs = (L + 1) * n * (8 + 4 + 8 + 8 + 4)
     tiles = (L + 1) * -(-n // 512)
-    teams = max(1, min(tiles, max(16, int(2.4e8 // (3 * 8 * 8 * max(n, 1))))))
-    bfs_state = teams * (3 * 8 * 8 + 3) * n
+    teams = max(1, min(tiles, max(16, int(2.4e8 // (2 * 8 * 8 * max(n, 1))))))
+    bfs_state = teams * (2 * 8 * 8 + 3) * n
     return int(csr + build + outputs + bfs_state + (1 << 20))
 
 

@@ -55,17 +55,17 @@ def test_footprint_grows_with_size():
 
 
 def test_footprint_covers_the_bfs_state_of_the_default_teams():
-    """The estimate holds the BFS state the library allocates by default: per team 3 arrays of
+    """The estimate holds the BFS state the library allocates by default: per team 2 snapshots of
     n x 8 words and 3 bytes per node, with at least 16 teams (no more than tiles), up to about
     240 MB of state in all."""
     serve = _mods()
-    per_node = 3 * 8 * 8 + 3
+    per_node = 2 * 8 * 8 + 3
     for n, layers in ((50000, 4), (200000, 2), (20000, 3), (3000, 2)):
         tiles = (layers + 1) * -(-n // 512)
-        teams = min(tiles, max(16, int(2.4e8 // (3 * 8 * 8 * n))))
+        teams = min(tiles, max(16, int(2.4e8 // (2 * 8 * 8 * n))))
         assert serve.footprint_bytes(n, [5 * n] * layers) >= teams * per_node * n
-    # 25 teams at n = 50,000 (the power-law workload), 16 at n = 200,000
-    assert serve.footprint_bytes(50000, [250000] * 4) >= 25 * per_node * 50000
+    # 37 teams at n = 50,000 (the power-law workload), 16 at n = 200,000
+    assert serve.footprint_bytes(50000, [250000] * 4) >= 37 * per_node * 50000
     assert serve.footprint_bytes(200000, [800000] * 4) >= 16 * per_node * 200000
 
 
