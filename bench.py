@@ -196,31 +196,31 @@ def peaks():
 PROFILE_FILES = {"powerlaw50k": "k_msbfs_powerlaw50k_launch.md", "ba200k": "k_msbfs_ba200k_launch.md"}
 
 
-def measured_traffic(workload: str, tiles: int, words: int, teams: int):
-    """DRAM bytes (read + write) per BFS launch from the committed ncu summary under profiles/,
-    scaled from the captured launch's tiles to this launch's; None when the kernel source, the
-    words per node or the team count differ from the capture's."""
+def measured_traffic(workload: str, tiles: int, words: int, teams: int, alpha: int):
+    """DRAM bytes (read + write) per BFS launch from the committed ncu summary under profiles/: the
+    capture of the same (words per node, teams, alpha) setting, scaled from its tiles to this launch's
+    (equal for the same workload). None when the kernel source changed since, or no capture has this
+    setting."""
     import hashlib
     if workload not in PROFILE_FILES:
         return None
     path = os.path.join(ROOT, "profiles", PROFILE_FILES[workload])
     src = os.path.join(ROOT, "paper_2207_11662_gb300", "csrc", "msbfs.cu")
     try:
-        kv = {}
-        with open(path) as f:
-            for line in f:
-                if ":" in line and not line.startswith(("|", "#", "`", " ")):
-                    k, v = line.split(":", 1)
-                    kv[k.strip()] = v.strip()
         with open(src, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        if kv.get("kernel_source_sha256_16") != sha:
-            return None
-        if int(kv["words_per_node"]) != int(words) or int(kv["teams"]) != int(teams):
-            return None
-        return int(int(kv["dram_bytes_launch"]) * tiles / int(kv["tiles_in_capture"]))
+        ok_sha = False
+        with open(path) as f:
+            for line in f:
+                if line.startswith("kernel_source_sha256_16:"):
+                    ok_sha = line.split(":", 1)[1].strip() == sha
+                if ok_sha and line.startswith("capture:"):
+                    kv = dict(x.split("=") for x in line.split(":", 1)[1].split())
+                    if (int(kv["words_per_node"]), int(kv["teams"]), int(kv["push_alpha"])) == (words, teams, alpha):
+                        return int(int(kv["dram_bytes_launch"]) * tiles / int(kv["tiles"]))
     except (OSError, KeyError, ValueError):
         return None
+    return None
 
 
 def bfs_bytes(prof: dict) -> float:
@@ -350,7 +350,8 @@ def roofline(workload, m, hp_tuning):
     launch_ms = m["bfs_ms"] / max(m["bfs_launches"], 1)
     achieved = alg_bytes_per_launch / (launch_ms / 1000.0) / 1e9
     hbm, peak_kind = peaks()
-    traffic = measured_traffic(workload, prof["batches"], prof["words_per_node"], prof["teams"])
+    traffic = measured_traffic(workload, prof["batches"], prof["words_per_node"], prof["teams"],
+                               hp_tuning.get("push_alpha", 16))
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
            "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
            "kernel": "k_msbfs (persistent all-sources BFS: every layer and the AND graph in one launch)",
@@ -718,9 +719,9 @@ def serving(args, dev):
     """Poisson stream (mean 50 req/s) of closeness/top-k queries on HoMLNs of 2-6 layers and
     1,000-100,000 nodes (log-uniform), ER or power-law layers of average degree 6-12, served by the
     continuous-batching server; latency = completion - arrival. The server's default (two workers:
-    small requests on a high-priority stream and 32 SMs, big ones on the other SMs, so that their work
-    overlaps on the device) and, on the same stream, one worker whose waves take the whole GPU in
-    arrival order."""
+    small requests on a high-priority stream, preempting the persistent BFS of a big request at a
+    tile boundary while their wave runs) and, on the same stream, one worker whose waves take the
+    whole GPU in arrival order."""
     import multiprocessing as mp
     from paper_2207_11662_gb300 import serve
     from paper_2207_11662_gb300 import synth
@@ -738,7 +739,9 @@ def serving(args, dev):
         out.update({"duration_s": round(wall, 2), "workers": srv.workers, "waves": srv.waves,
                     "errors": srv.errors[:3]})
         if srv.workers >= 2:
-            out["small_sms"] = srv.small_sms
+            out["preemptions"] = srv.preemptions
+            if srv.small_sms:
+                out["small_sms"] = srv.small_sms
         return out
 
     out = run()
@@ -808,9 +811,11 @@ def summary(result: dict) -> dict:
     if v:
         out["serving"] = {k: v[k] for k in ("p50_ms", "p90_ms", "p99_ms", "req_per_s") if k in v}
         out["serving"]["small_p99_ms"] = v["small"]["p99_ms"]
+        out["serving"]["big_p99_ms"] = v["big"]["p99_ms"]
         one = v.get("one_worker_whole_gpu")
         if one:
             out["serving"]["one_worker"] = {k: one[k] for k in ("p50_ms", "p90_ms", "p99_ms")}
+            out["serving"]["one_worker"]["small_p99_ms"] = one["small"]["p99_ms"]
     return out
 
 

@@ -51,6 +51,7 @@ extern "C" {
 
 /* Opaque handle of a captured analysis (homln_graph_capture). */
 typedef struct homln_graph_s *homln_graph_t;
+typedef struct homln_yield_s *homln_yield_t;
 
 /* Opaque handle: one HoMLN resident on one GPU. */
 typedef struct homln_s *homln_t;
@@ -341,6 +342,29 @@ typedef struct homln_profile_t {
     int32_t words_per_node;     /* W of the last instrumented launch */
     int32_t teams;              /* teams of the last instrumented launch */
 } homln_profile_t;
+
+/* Preemption of the persistent BFS, for serving (the paper has no counterpart: it concerns how
+ * several requests share one GPU). A yield flag is one int32 in pinned host memory that the GPU
+ * reads directly.
+ *   homln_yield_create   allocate a flag, lowered (0). Errors: EINVAL (out NULL), ECUDA.
+ *   homln_yield_destroy  free it; no handle may still watch it (NULL is accepted).
+ *   homln_yield_set      raise (nonzero) or lower (0) the flag; callable from any host thread.
+ *   homln_yield_count    how many times BFS launches watching the flag stopped early for it.
+ *   homln_set_yield      the persistent BFS of calls led by handle h (its analyses, and batches
+ *                        whose first handle is h) watches flag y (NULL: none). While y is raised
+ *                        the BFS hands out no new (graph, batch) tile: the running launch ends
+ *                        after the tiles it has started, the calling host thread waits until y
+ *                        is lowered (at most 60 s, then HOMLN_ETIMEOUT), and a new launch resumes
+ *                        the remaining tiles. Results are identical. Such calls wait for each BFS
+ *                        launch to end before returning, and a handle that watches a flag cannot
+ *                        be captured in a CUDA graph (EINVAL). homln_set_tuning keeps the flag.
+ * Typical use: the worker of large requests watches the flag; the worker of small requests raises
+ * it while its own wave runs, so small requests do not wait for a large one to finish. */
+HOMLN_API homln_status homln_yield_create(homln_yield_t *out);
+HOMLN_API homln_status homln_yield_destroy(homln_yield_t y);
+HOMLN_API homln_status homln_yield_set(homln_yield_t y, int32_t raised);
+HOMLN_API homln_status homln_yield_count(homln_yield_t y, int64_t *out);
+HOMLN_API homln_status homln_set_yield(homln_t h, homln_yield_t y);
 
 HOMLN_API homln_status homln_set_profiling(homln_t h, int32_t timing, int32_t instrument);
 HOMLN_API homln_status homln_get_profile(homln_t h, homln_profile_t *out);

@@ -624,6 +624,61 @@ const char *homln_last_error(void) { return g_last_error.c_str(); }
 
 const char *homln_version(void) { return "homln-gb300 0.1 (sm_103a)"; }
 
+// One int32 in pinned host memory, mapped into the device's address space.
+struct homln_yield_s {
+    int32_t *host = nullptr;
+    int32_t *dev = nullptr;
+    std::atomic<long long> count{0};
+    ~homln_yield_s() {
+        if (host) cudaFreeHost(host);
+    }
+};
+
+homln_status homln_yield_create(homln_yield_t *out) {
+    API_BEGIN
+    if (!out) fail(HOMLN_EINVAL, "out is NULL");
+    auto y = std::make_unique<homln_yield_s>();
+    void *p = nullptr;
+    HCUDA(cudaHostAlloc(&p, 64, cudaHostAllocMapped | cudaHostAllocPortable));
+    y->host = static_cast<int32_t *>(p);
+    __atomic_store_n(y->host, 0, __ATOMIC_RELEASE);
+    void *d = nullptr;
+    HCUDA(cudaHostGetDevicePointer(&d, p, 0));
+    y->dev = static_cast<int32_t *>(d);
+    *out = y.release();
+    API_END
+}
+
+homln_status homln_yield_destroy(homln_yield_t y) {
+    API_BEGIN
+    delete y;
+    API_END
+}
+
+homln_status homln_yield_set(homln_yield_t y, int32_t raised) {
+    API_BEGIN
+    if (!y) fail(HOMLN_EINVAL, "yield flag is NULL");
+    __atomic_store_n(y->host, raised ? 1 : 0, __ATOMIC_SEQ_CST);
+    API_END
+}
+
+homln_status homln_yield_count(homln_yield_t y, int64_t *out) {
+    API_BEGIN
+    if (!y || !out) fail(HOMLN_EINVAL, "yield flag and out are required");
+    *out = (int64_t)y->count.load();
+    API_END
+}
+
+homln_status homln_set_yield(homln_t h, homln_yield_t y) {
+    API_BEGIN
+    if (!h) fail(HOMLN_EINVAL, "handle is NULL");
+    if (h->live_graphs > 0) fail(HOMLN_EBUSY, "a captured graph uses this handle");
+    h->tuning.yield_host = y ? y->host : nullptr;
+    h->tuning.yield_dev = y ? y->dev : nullptr;
+    h->tuning.yield_count = y ? &y->count : nullptr;
+    API_END
+}
+
 homln_status homln_create(int32_t n_nodes, int32_t n_layers, const int64_t *edge_counts, const int32_t *const *src,
                           const int32_t *const *dst, uint32_t flags, const homln_allocator *alloc, void *stream,
                           homln_t *out) {
@@ -729,6 +784,9 @@ homln_status homln_set_tuning(homln_t h, const homln_tuning *t) {
         if (t->sm_count < 0) fail(HOMLN_EINVAL, "sm_count must be >= 0");
         bt.sm_count = t->sm_count;
     }
+    bt.yield_host = h->tuning.yield_host;  // the yield flag is set apart (homln_set_yield)
+    bt.yield_dev = h->tuning.yield_dev;
+    bt.yield_count = h->tuning.yield_count;
     h->tuning = bt;
     API_END
 }
@@ -848,6 +906,7 @@ homln_status homln_graph_capture(homln_t *nets, int32_t count, const uint64_t *m
         if (nets[i]->device != h->device) fail(HOMLN_EINVAL, "all handles must live on one device");
     if (h->tuning.schedule == 1) fail(HOMLN_EINVAL, "the plain schedule cannot be captured (the host drives it)");
     if (h->instrument) fail(HOMLN_EINVAL, "an instrumented handle cannot be captured");
+    if (h->tuning.yield_dev) fail(HOMLN_EINVAL, "a handle that watches a yield flag cannot be captured");
     use_device(h);
     Items items;
     for (int32_t i = 0; i < count; ++i) {

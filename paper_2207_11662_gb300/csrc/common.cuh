@@ -269,6 +269,12 @@ struct BfsTuning {
     int phantom = 0;           // tests: team barriers also wait for blocks that do not exist
     int max_tiles = 0;         // persistent launches take at most this many tiles each (0 = all)
     int sm_count = 0;          // persistent launches size their grid for this many SMs (0 = all)
+    // preemption (homln_set_yield): while *yield_host != 0 the persistent BFS hands out no more
+    // tiles (its kernel reads the flag through yield_dev) and stops after the tiles it runs; the
+    // host resumes the remaining tiles once the flag is 0 again and counts the stop in yield_count
+    const volatile int32_t *yield_host = nullptr;
+    const int32_t *yield_dev = nullptr;
+    std::atomic<long long> *yield_count = nullptr;
     int shard_rank = 0;        // only source batches shard_rank, shard_rank + shard_world, ...
     int shard_world = 1;       //   (partial F/R of a sharded analysis; 0 / 1 = all sources)
 };

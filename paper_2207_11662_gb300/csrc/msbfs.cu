@@ -27,7 +27,9 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <memory>
+#include <thread>
 
 namespace homln {
 
@@ -75,6 +77,8 @@ struct TeamArgs {
     unsigned long long *stats;
     uint64_t wait_ns;           // give-up time of every barrier wait
     int32_t phantom;            // tests: blocks every team barrier waits for in vain
+    const int32_t *yield;       // preemption flag in mapped host memory (nullptr: none): while it is
+                                // nonzero, teams take no new tile and the launch ends
 };
 
 // First vertex of a degree-descending vertex range 0 .. n-1 whose degree is below thr (binary search).
@@ -885,7 +889,12 @@ __global__ void __launch_bounds__(HOMLN_BFS_MAX_THREADS, HOMLN_BFS_MIN_BLOCKS) k
     uint32_t ps = 0;
     bool ok = true;
     while (ok) {
-        if (rank == 0 && threadIdx.x == 0) *tile_slot = atomicAdd(A.queue, 1);
+        if (rank == 0 && threadIdx.x == 0) {
+            // a raised yield flag ends the launch before the next tile is taken, so every tile handed
+            // out is finished and the queue counter tells the host where to resume
+            if (A.yield && *reinterpret_cast<const volatile int32_t *>(A.yield) != 0) *tile_slot = A.ntiles;
+            else *tile_slot = atomicAdd(A.queue, 1);
+        }
         if (!team_sync(tb)) break;
         const int32_t t = *tile_slot;
         if (t >= A.ntiles) break;
@@ -1217,12 +1226,23 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
     A.stats = stats ? p->st.p : nullptr;
     A.wait_ns = (uint64_t)t.wait_limit_ms * 1000000ull;
     A.phantom = t.phantom;
+    A.yield = plain ? nullptr : t.yield_dev;
     return p.release();
 }
 
 void bfs_plan_destroy(BfsPlan *p) { delete p; }
 
-bool bfs_plan_capturable(const BfsPlan *p) { return p && !p->plain && !p->stats; }
+bool bfs_plan_capturable(const BfsPlan *p) { return p && !p->plain && !p->stats && !p->A.yield; }
+
+// Host side of a yield: block until the flag is 0 again (bounded: HOMLN_ETIMEOUT after 60 s).
+static void wait_yield_cleared(const BfsTuning &t) {
+    const auto t0 = std::chrono::steady_clock::now();
+    while (*t.yield_host != 0) {
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+            fail(HOMLN_ETIMEOUT, "the yield flag stayed raised for 60 s");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
 
 void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
     if (!p) return;
@@ -1242,17 +1262,34 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
     if (ev_start) HCUDA(cudaEventRecord(ev_start, s));
     if (!p->plain) {
         // max_tiles: the tiles go out in several launches of at most that many, so that work of
-        // other streams (a higher-priority one, say) can run in between
+        // other streams (a higher-priority one, say) can run in between. With a yield flag, a
+        // launch that stopped early (the flag was raised) is resumed from the queue counter once
+        // the flag is 0 again; the host waits for each launch to end to read the counter.
         const int32_t chunk = p->t.max_tiles > 0 ? p->t.max_tiles : tile;
-        for (int32_t c0 = 0; c0 < tile; c0 += chunk) {
-            if (c0 > 0) {  // fresh barriers, counters and team formation; the queue resumes at c0
+        int32_t c0 = 0;
+        bool first = true;
+        while (c0 < tile) {
+            if (!first) {  // fresh barriers, counters and team formation; the queue resumes at c0
                 HCUDA(cudaMemsetAsync(p->ctr.p, 0, 16 * nteams * sizeof(unsigned long long), s));
                 HCUDA(cudaMemsetAsync(p->barmem.p, 0, p->bar_words * sizeof(uint32_t), s));
                 launch(k_set_i32, 1, 1, 0, s, p->queue.p, c0);
             }
+            first = false;
             A.ntiles = (int32_t)std::min<int64_t>(tile, (int64_t)c0 + chunk);
             g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
             HCUDA(cudaLaunchCooperativeKernel((const void *)p->kern, dim3(grid), dim3(threads), args, 0, s));
+            if (A.yield) {
+                int32_t handed = 0;  // tiles handed out, all of them finished
+                HCUDA(cudaMemcpyAsync(&handed, p->queue.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                HCUDA(cudaStreamSynchronize(s));
+                if (handed < A.ntiles) {
+                    if (p->t.yield_count) p->t.yield_count->fetch_add(1, std::memory_order_relaxed);
+                    wait_yield_cleared(p->t);
+                    c0 = std::max(c0, handed);
+                    continue;
+                }
+            }
+            c0 = A.ntiles;
         }
     } else {
         // plain schedule: one launch per phase, the host reads the level counters after every level

@@ -35,7 +35,8 @@ EXPORTS = [
     "homln_version", "homln_accuracy_noalloc", "homln_analyse", "homln_batch_analyse", "homln_invalidate",
     "homln_subset_sweep", "homln_or_aggregate", "homln_or_closeness", "homln_export_partials",
     "homln_import_partials", "homln_graph_capture", "homln_graph_launch", "homln_graph_destroy",
-    "homln_shard_partials", "homln_batch_closeness",
+    "homln_shard_partials", "homln_batch_closeness", "homln_yield_create", "homln_yield_destroy",
+    "homln_yield_set", "homln_yield_count", "homln_set_yield",
 ]
 
 
@@ -128,6 +129,11 @@ def _load():
         "homln_version": (c_char_p, []),
         "homln_accuracy_noalloc": (S, [c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                        POINTER(homln_accuracy_t)]),
+        "homln_yield_create": (S, [POINTER(c_void_p)]),
+        "homln_yield_destroy": (S, [c_void_p]),
+        "homln_yield_set": (S, [c_void_p, c_int32]),
+        "homln_yield_count": (S, [c_void_p, POINTER(c_int64)]),
+        "homln_set_yield": (S, [c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -328,6 +334,33 @@ def homln_accuracy_noalloc(n_nodes: int, pred, n_pred: int, truth, n_truth: int,
                                       c_void_p(stream) if stream else None, ctypes.byref(out)),
            "homln_accuracy_noalloc")
     return out.as_dict()
+
+
+def homln_yield_create():
+    """A lowered yield flag (pinned host memory the GPU reads): see homln_set_yield."""
+    y = c_void_p()
+    _check(lib.homln_yield_create(ctypes.byref(y)), "homln_yield_create")
+    return y.value
+
+
+def homln_yield_destroy(y) -> None:
+    _check(lib.homln_yield_destroy(y), "homln_yield_destroy")
+
+
+def homln_yield_set(y, raised: bool) -> None:
+    _check(lib.homln_yield_set(y, int(bool(raised))), "homln_yield_set")
+
+
+def homln_yield_count(y) -> int:
+    out = c_int64()
+    _check(lib.homln_yield_count(y, ctypes.byref(out)), "homln_yield_count")
+    return int(out.value)
+
+
+def homln_set_yield(h, y) -> None:
+    """The persistent BFS of calls led by h stops handing out tiles while y is raised and resumes
+    once it is lowered (identical results; the call waits for each launch to end)."""
+    _check(lib.homln_set_yield(h, y), "homln_set_yield")
 
 
 def homln_set_profiling(h, timing: bool, instrument: bool = False) -> None:

@@ -15,14 +15,16 @@ Scheduling:
     tiles of the wave (homln_batch_analyse), then selection, composition and
     accuracy. Requests that arrive while a wave is on the GPU join the next wave of
     a free worker;
-  * size classes and overlap on the device: a request is "big" when its BFS work
-    (nodes x edges) exceeds ``big_work``. With two or more workers (the default is
-    two), worker 0 serves only small requests, on a high-priority stream, and its
-    persistent BFS launches are sized for ``small_sms`` SMs; the other workers take
-    big requests first (then small ones) and size theirs for the remaining SMs. So a
-    small request that arrives while a big one is on the GPU starts at once: its
-    kernels run beside the big request's BFS instead of waiting for it to end.
-    With one worker every wave takes the whole GPU, in arrival order.
+  * size classes and preemption: a request is "big" when its BFS work (nodes x edges)
+    exceeds ``big_work``. With two or more workers (the default is two), worker 0 serves
+    only small requests, on a high-priority stream; the other workers take big requests
+    first (then small ones). The big waves' persistent BFS watches a yield flag
+    (homln_set_yield) that worker 0 raises while one of its waves runs: the big BFS then
+    finishes the tiles it has started, gives the GPU to the small wave and resumes its
+    remaining tiles when the flag is lowered. So a small request that arrives while a big
+    one is on the GPU waits about one BFS tile, not the whole big request. (``small_sms``
+    instead splits the GPU by SMs between the two kinds of waves, without preemption;
+    measured slower.) With one worker every wave takes the whole GPU, in arrival order.
 
 Every GPU step runs in libhomln.so; this module only schedules.
 """
@@ -156,7 +158,7 @@ def work_estimate(n: int, edge_counts) -> int:
 class Server:
     def __init__(self, device: int = 0, workers: int = 2, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
                  percent: float = 10.0, keep_farness: bool = False, tuning: dict | None = None,
-                 big_work: float = 2e10, small_sms: int = 32, big_max_tiles: int = 0):
+                 big_work: float = 2e10, preempt: bool = True, small_sms: int = 0, big_max_tiles: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -164,8 +166,13 @@ class Server:
         self.max_wave = max_wave
         self.big_work = big_work
         self.nsm = torch.cuda.get_device_properties(self.device).multi_processor_count
-        self.small_sms = max(1, min(int(small_sms), self.nsm - 1))
+        self.small_sms = max(0, min(int(small_sms), self.nsm - 1))
+        self.preempt = bool(preempt) and workers >= 2 and self.small_sms == 0
         self.big_max_tiles = big_max_tiles
+        self._yield = None          # the yield flag big waves watch (preempt)
+        self._small_active = 0      # small waves running; the flag is raised while > 0
+        self._ylock = threading.Lock()
+        self.preemptions = 0
         self.adm = Admission(mem_budget_bytes)
         self.sel = H.make_select(H.HOMLN_TOPK_PERCENT, percent)
         self.keep_farness = keep_farness
@@ -177,16 +184,27 @@ class Server:
         self.errors = []
 
     # ---------------------------------------------------------------- workers
-    def _run_wave(self, items, stream, wave_id, tuning):
+    def _small_wave(self, start: bool):
+        """Raise the yield flag while at least one small wave runs."""
+        with self._ylock:
+            self._small_active += 1 if start else -1
+            H.homln_yield_set(self._yield, self._small_active > 0)
+
+    def _run_wave(self, items, stream, wave_id, tuning, small_only=False):
         reqs = [r for r, _ in items]
         t_admit = time.perf_counter() - self.t0
         handles = []
+        preempting = self._yield is not None and small_only
+        if preempting:
+            self._small_wave(True)
         try:
             for r in reqs:
                 r.t_admit = t_admit
                 r.wave = wave_id
                 handles.append(H.homln_create(r.n, r.layers, stream=stream.cuda_stream))
             H.homln_set_tuning(handles[0], **tuning)
+            if self._yield is not None and not small_only:
+                H.homln_set_yield(handles[0], self._yield)
             masks = [(1 << len(r.layers)) - 1 for r in reqs]
             H.homln_batch_analyse(handles, masks, True)
             for r, h, mask in zip(reqs, handles, masks):
@@ -212,6 +230,8 @@ class Server:
         finally:
             for h in handles:
                 H.homln_destroy(h)
+            if preempting:
+                self._small_wave(False)
             t_done = time.perf_counter() - self.t0
             for r, need in items:
                 r.t_done = t_done
@@ -222,16 +242,16 @@ class Server:
     def _worker(self, idx):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        # worker 0 of two or more serves small requests only, at high priority, on small_sms SMs'
-        # worth of BFS blocks; the others take big requests first on the rest of the GPU
+        # worker 0 of two or more serves small requests only, at high priority (preempting the big
+        # waves, or on small_sms SMs' worth of BFS blocks); the others take big requests first
         small_only = self.workers >= 2 and idx == 0
         classes = (SMALL,) if small_only else (BIG, SMALL) if self.workers >= 2 else None
         stream = torch.cuda.Stream(self.device, priority=-1 if small_only else 0)
         tuning = dict(self.tuning)
-        if self.workers >= 2:
+        if self.workers >= 2 and self.small_sms:
             tuning.setdefault("sm_count", self.small_sms if small_only else self.nsm - self.small_sms)
-            if not small_only and self.big_max_tiles:
-                tuning.setdefault("max_tiles_per_launch", self.big_max_tiles)
+        if not small_only and self.big_max_tiles:
+            tuning.setdefault("max_tiles_per_launch", self.big_max_tiles)
         while True:
             items = self.adm.take(self.max_wave, timeout=0.05, classes=classes)
             if items is None:
@@ -242,7 +262,7 @@ class Server:
                 wave_id = self.waves
                 self.waves += 1
             try:
-                self._run_wave(items, stream, wave_id, tuning)
+                self._run_wave(items, stream, wave_id, tuning, small_only)
             except Exception as e:  # keep serving; record the failure
                 self.errors.append(repr(e))
 
@@ -261,6 +281,10 @@ class Server:
         """Replay the requests at their arrival times (or all at once) and serve them; returns them done."""
         self.t0 = time.perf_counter()
         self.done = []
+        if self.preempt:
+            self.torch.cuda.set_device(self.device)
+            self._yield = H.homln_yield_create()
+            self._small_active = 0
         threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(self.workers)]
         for t in threads:
             t.start()
@@ -274,6 +298,10 @@ class Server:
         for t in threads:
             t.join()
         self.torch.cuda.synchronize(self.device)
+        if self._yield is not None:
+            self.preemptions = H.homln_yield_count(self._yield)
+            H.homln_yield_destroy(self._yield)
+            self._yield = None
         return sorted(self.done, key=lambda r: r.rid)
 
 

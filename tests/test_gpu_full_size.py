@@ -179,3 +179,48 @@ def test_paper_shaped_network_matches_oracle(H, golden):
     sels = {f"ge_mean_theta{t}": H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=t) for t in G.PARMAT_THETAS}
     check_network(H, g, net.n_layers, ent, sels, tag="parmat50k")
     g.close()
+
+
+def test_yield_flag_stops_and_resumes_the_bfs(H, golden):
+    """Preemption for serving: with the yield flag raised the persistent BFS hands out no tile and its
+    launch ends; once lowered, the remaining tiles run in a new launch. Raised before the analysis and
+    toggled every few milliseconds during it, the flag must cost nothing in correctness: every output
+    equals the oracle's full run, and the stops are counted."""
+    import threading
+    import time
+    net = synth.homln_powerlaw()
+    ent = golden["powerlaw50k"]
+    check_inputs(net, ent)
+    y = H.homln_yield_create()
+    g = H.Network(net.n, to_dev(net.layers), tuning=dict(words_per_node=4))  # 4 x 196 + 196 tiles
+    try:
+        H.homln_set_yield(g.h, y)
+        H.homln_yield_set(y, True)  # raised before the analysis starts: the first launch stops at once
+        done = threading.Event()
+
+        def toggle():
+            time.sleep(0.2)
+            H.homln_yield_set(y, False)
+            while not done.is_set():
+                time.sleep(0.003)
+                H.homln_yield_set(y, True)
+                time.sleep(0.001)
+                H.homln_yield_set(y, False)
+
+        t = threading.Thread(target=toggle)
+        t.start()
+        try:
+            g.analyse((1 << net.n_layers) - 1, True)
+        finally:
+            done.set()
+            t.join()
+        H.homln_yield_set(y, False)
+        assert H.homln_yield_count(y) >= 1
+        check_network(H, g, net.n_layers, ent, {"top10": sels_of(H)["top10"]}, heuristics=("cc2",), tag="yield")
+        with pytest.raises(H.HomlnError) as err:  # a watching handle cannot be captured
+            H.homln_graph_capture([g.h], [(1 << net.n_layers) - 1], True)
+        assert err.value.code == H.HOMLN_EINVAL
+        H.homln_set_yield(g.h, None)
+    finally:
+        g.close()
+        H.homln_yield_destroy(y)

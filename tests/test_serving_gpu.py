@@ -50,7 +50,7 @@ def test_alone_equals_mix_and_oracle():
     torch.cuda.set_device(0)
     G, ents, make = golden_requests(serve)
     alone = serve.Server(workers=1, max_wave=1, keep_farness=True).run(make(), realtime=False)
-    srv = serve.Server(keep_farness=True, max_wave=5)  # the default: overlapping small and big waves
+    srv = serve.Server(keep_farness=True, max_wave=5)  # the default: small waves preempt big ones
     mix = srv.run(make(), realtime=False)
     assert srv.waves >= 3 and not srv.errors
     for a, b, ent in zip(alone, mix, ents):
