@@ -101,8 +101,9 @@ def make_workload(name: str, rank: int):
     return net, desc
 
 
-def teps_work(n: int, layers) -> int:
-    """sum over analysed graphs of sum_s |E(comp(s))| = sum over components of n_c * m_c."""
+def teps_work(n: int, layers, want_per_graph: bool = False):
+    """sum over analysed graphs of sum_s |E(comp(s))| = sum over components of n_c * m_c (and, with
+    want_per_graph, the same per graph: every layer, then the AND graph)."""
     import scipy.sparse as sps
     from scipy.sparse.csgraph import connected_components
 
@@ -117,15 +118,17 @@ def teps_work(n: int, layers) -> int:
     inter = keys[0]
     for k in keys[1:]:
         inter = np.intersect1d(inter, k, assume_unique=True)
-    total = 0
+    per_graph = []
     for k in keys + [inter]:
         lo, hi = k // n, k % n
         A = sps.coo_matrix((np.ones(lo.shape[0]), (lo, hi)), shape=(n, n)).tocsr()
         nc, lab = connected_components(A, directed=False)
         nodes = np.bincount(lab, minlength=nc).astype(np.int64)
         edges = np.bincount(lab[lo], minlength=nc).astype(np.int64)
-        total += int(np.sum(nodes * edges))
-    return total, [int(k.shape[0]) for k in keys + [inter]]
+        per_graph.append(int(np.sum(nodes * edges)))
+    if want_per_graph:
+        return sum(per_graph), [int(k.shape[0]) for k in keys + [inter]], per_graph
+    return sum(per_graph), [int(k.shape[0]) for k in keys + [inter]]
 
 
 class ClockSampler:
@@ -196,11 +199,11 @@ def peaks():
 PROFILE_FILES = {"powerlaw50k": "k_msbfs_powerlaw50k_launch.md", "ba200k": "k_msbfs_ba200k_launch.md"}
 
 
-def measured_traffic(workload: str, tiles: int, words: int, teams: int, alpha: int):
+def measured_traffic(workload: str, tiles: int, words: int, teams: int, alpha: int, mix: int = 0):
     """DRAM bytes (read + write) per BFS launch from the committed ncu summary under profiles/: the
-    capture of the same (words per node, teams, alpha) setting, scaled from its tiles to this launch's
-    (equal for the same workload). None when the kernel source changed since, or no capture has this
-    setting."""
+    capture of the same (words per node, teams, alpha, team mix) setting, scaled from its tiles to
+    this launch's (equal for the same workload). None when the kernel source changed since, or no
+    capture has this setting."""
     import hashlib
     if workload not in PROFILE_FILES:
         return None
@@ -216,7 +219,8 @@ def measured_traffic(workload: str, tiles: int, words: int, teams: int, alpha: i
                     ok_sha = line.split(":", 1)[1].strip() == sha
                 if ok_sha and line.startswith("capture:"):
                     kv = dict(x.split("=") for x in line.split(":", 1)[1].split())
-                    if (int(kv["words_per_node"]), int(kv["teams"]), int(kv["push_alpha"])) == (words, teams, alpha):
+                    key = (int(kv["words_per_node"]), int(kv["teams"]), int(kv["push_alpha"]), int(kv.get("team_mix", 0)))
+                    if key == (words, teams, alpha, mix):
                         return int(int(kv["dram_bytes_launch"]) * tiles / int(kv["tiles"]))
     except (OSError, KeyError, ValueError):
         return None
@@ -351,7 +355,7 @@ def roofline(workload, m, hp_tuning):
     achieved = alg_bytes_per_launch / (launch_ms / 1000.0) / 1e9
     hbm, peak_kind = peaks()
     traffic = measured_traffic(workload, prof["batches"], prof["words_per_node"], prof["teams"],
-                               hp_tuning.get("push_alpha", 16))
+                               hp_tuning.get("push_alpha", 16), hp_tuning.get("team_mix", 0))
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
            "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
            "kernel": "k_msbfs (persistent all-sources BFS: every layer and the AND graph in one launch)",
@@ -360,6 +364,35 @@ def roofline(workload, m, hp_tuning):
     if traffic:
         out["dram_gbs"] = round(traffic / (launch_ms / 1000.0) / 1e9, 1)
         out["dram_frac"] = round(out["dram_gbs"] / hbm, 4)
+    return out
+
+
+def per_graph_teps(H, net, dev, stream, tuning, per_graph_work, reps=3):
+    """Each layer's and the AND graph's all-sources BFS in a launch of its own (a fresh handle each,
+    best of reps), CUDA-event timed around the launch: GTEPS per graph."""
+    import torch
+    n, L = net.n, net.n_layers
+    layers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
+    F = torch.empty(n, dtype=torch.int64, device=dev)
+    out = []
+    for g in range(L + 1):
+        best = float("inf")
+        for _ in range(reps):
+            h = H.homln_create(n, layers, stream=stream.cuda_stream)
+            try:
+                if tuning:
+                    H.homln_set_tuning(h, **tuning)
+                H.homln_set_profiling(h, True, False)
+                if g < L:
+                    H.homln_layer_closeness(h, g, F, None, None)
+                else:
+                    H.homln_and_closeness(h, (1 << L) - 1, F, None, None)
+                torch.cuda.synchronize()
+                best = min(best, H.homln_get_profile(h)["bfs_ms"])
+            finally:
+                H.homln_destroy(h)
+        out.append({"graph": f"layer {g}" if g < L else "AND", "bfs_ms": round(best, 3),
+                    "gteps": round(per_graph_work[g] / best / 1e6, 1)})
     return out
 
 
@@ -394,7 +427,7 @@ def run_ours(args, rank, world, dist):
         hp.step(dlayers)
         torch.cuda.synchronize()
         return None, net
-    work, edge_counts = teps_work(n, net.layers)
+    work, edge_counts, work_per_graph = teps_work(n, net.layers, want_per_graph=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     m = measure(H, hp, dev, args.steps, args.warmup, flush, dist, sample_clocks=True)
     t_local = sum(m["step_ms"]) / 1000.0
@@ -418,6 +451,7 @@ def run_ours(args, rank, world, dist):
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
     d2h = (L + 1) * n * (8 + 4 + 8) + 4 * n * 4
     e2e_units, e2e_t = job_aggregate(work * args.steps, sum(e2e_ms) / 1000.0, dist, dev)
+    per_graph = per_graph_teps(H, net, dev, stream, tuning, work_per_graph) if rank == 0 else None
 
     prof_count = m["prof_count"]
     result = {
@@ -442,11 +476,12 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": int(m["launches"]),
         "clocks": m["clocks"],
         "tuning": {"chosen": {"words_per_node": prof_count["words_per_node"], "teams": prof_count["teams"],
-                              "push_alpha": tuning.get("push_alpha", 16)},
+                              "push_alpha": tuning.get("push_alpha", 16), "team_mix": tuning.get("team_mix", 0)},
                    "source": "autotuner" if tune_log else ("flags" if tuning else "library defaults"),
                    "candidates_timed": len(tune_log["candidates"]) if tune_log else 0,
                    "reps": tune_log["reps"] if tune_log else 0,
                    "top": tune_log["candidates"][:4] if tune_log else []},
+        "per_graph": per_graph,
         "accuracy_vs_ground_truth": {nm: {k: round(a[k], 4) for k in ("jaccard", "precision", "recall", "f1")}
                                      for nm, a in zip(("naive", "cc1", "cc2"), m["accs"])},
         "bfs_profile": {k: prof_count[k] for k in ("levels", "pull_levels", "push_levels", "batches",
@@ -474,7 +509,7 @@ def secondary_config(args, name, dev, steps=10, warmup=3):
     return {"workload": desc, "gteps": round(work * steps / t / 1e9, 3), "ms_per_step": round(t * 1000.0 / steps, 3),
             "steps": steps, "roofline": roofline(name, m, tuning),
             "tuning": {"words_per_node": pc["words_per_node"], "teams": pc["teams"],
-                       "push_alpha": tuning.get("push_alpha", 16)}}
+                       "push_alpha": tuning.get("push_alpha", 16), "team_mix": tuning.get("team_mix", 0)}}
 
 
 def batch_vs_plain(args, dev):
@@ -753,39 +788,48 @@ def serving(args, dev):
     return out
 
 
-def cpu_baseline(net, sources_per_graph: int, seed: int = 2001, one_core_sources: int = 0):
-    """The oracle as it stands: queue BFS from a seeded sample of sources on every analysed graph,
-    OpenMP over the host's cores (and, with one_core_sources, a smaller sample on one core)."""
-    from oracle import oracle as O
-    n = net.n
-    keys = [O.edge_keys(n, s, d) for s, d in net.layers]
-    graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
-    threads = os.cpu_count() or 1
-    import scipy.sparse as sps
-    from scipy.sparse.csgraph import connected_components
-    comp = []
-    for rp, col in graphs:
-        A = sps.csr_matrix((np.ones(col.shape[0]), col, rp), shape=(n, n))
-        nc, lab = connected_components(A, directed=False)
-        comp.append((lab, np.bincount(lab, weights=np.diff(rp), minlength=nc) / 2))
+class OracleSample:
+    """The oracle as it stands: queue BFS from a seeded sample of sources on every analysed graph
+    (the layers and their AND graph, built once), OpenMP over the host's cores."""
 
-    def run(count, nthreads, rng):
+    def __init__(self, net):
+        from oracle import oracle as O
+        import scipy.sparse as sps
+        from scipy.sparse.csgraph import connected_components
+        self.O = O
+        self.n = n = net.n
+        keys = [O.edge_keys(n, s, d) for s, d in net.layers]
+        self.graphs = [O.csr_from_keys(n, k) for k in keys] + [O.csr_from_keys(n, O.and_keys(n, keys))]
+        self.comp = []
+        for rp, col in self.graphs:
+            A = sps.csr_matrix((np.ones(col.shape[0]), col, rp), shape=(n, n))
+            nc, lab = connected_components(A, directed=False)
+            self.comp.append((lab, np.bincount(lab, weights=np.diff(rp), minlength=nc) / 2))
+
+    def run(self, count, nthreads, rng):
+        """GTEPS of the sample (edges of the sources' components / BFS wall time) and the seconds."""
         work, t = 0, 0.0
-        for (rp, col), (lab, m_comp) in zip(graphs, comp):
-            src = np.sort(rng.choice(n, min(count, n), replace=False)).astype(np.int32)
+        for (rp, col), (lab, m_comp) in zip(self.graphs, self.comp):
+            src = np.sort(rng.choice(self.n, min(count, self.n), replace=False)).astype(np.int32)
             work += int(np.sum(m_comp[lab[src]]))
             t0 = time.perf_counter()
-            O.farness_reach(n, rp, col, sources=src, threads=nthreads)
+            self.O.farness_reach(self.n, rp, col, sources=src, threads=nthreads)
             t += time.perf_counter() - t0
         return work / t / 1e9, t
 
-    value, t = run(sources_per_graph, threads, np.random.default_rng(seed))
+
+def cpu_baseline(net, sources_per_graph: int, seed: int = 2001, one_core_sources: int = 0, sampler=None):
+    """The oracle timed on the host cores on a seeded sample of sources per graph (and, with
+    one_core_sources, a smaller sample on one core)."""
+    sampler = sampler or OracleSample(net)
+    threads = os.cpu_count() or 1
+    value, t = sampler.run(sources_per_graph, threads, np.random.default_rng(seed))
     out = {"value": round(value, 4), "unit": "GTEPS", "cores": threads, "kind": "oracle",
-           "sample": f"queue BFS from {sources_per_graph} seeded sources on each of the {len(graphs)} graphs "
+           "sample": f"queue BFS from {sources_per_graph} seeded sources on each of the {len(sampler.graphs)} graphs "
                      f"(4 layers + AND), {t:.1f} s wall on {threads} threads ({t * threads:.0f} core-seconds), "
                      f"OpenMP over sources"}
     if one_core_sources:
-        v1, t1 = run(one_core_sources, 1, np.random.default_rng(seed + 1))
+        v1, t1 = sampler.run(one_core_sources, 1, np.random.default_rng(seed + 1))
         out["one_core_value"] = round(v1, 4)
         out["one_core_sample"] = f"{one_core_sources} seeded sources per graph on 1 thread, {t1:.1f} s"
     return out
@@ -828,12 +872,14 @@ def main():
         if rank != 0:
             return
         net, desc = make_workload(args.workload, 0)
+        sampler = OracleSample(net)  # the graphs are built once; a step is one bounded BFS sample
+        per_step = max(1, args.cpu_sample_sources // 2)
         for _ in range(args.warmup):
-            cpu_baseline(net, max(50, args.cpu_sample_sources // 10))
+            cpu_baseline(net, max(50, per_step // 10), sampler=sampler)
         vals, secs = [], []
         for k in range(args.steps):
             t0 = time.perf_counter()
-            vals.append(cpu_baseline(net, args.cpu_sample_sources, seed=2001 + k))
+            vals.append(cpu_baseline(net, per_step, seed=2001 + k, sampler=sampler))
             secs.append(time.perf_counter() - t0)
         v = statistics.mean(x["value"] for x in vals)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GTEPS",
@@ -869,7 +915,8 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(net, args.cpu_sample_sources, one_core_sources=150)
         # headline keys first, the long detail next, the summary last
-        head = {k: result.pop(k) for k in list(result) if k not in ("accuracy_vs_ground_truth", "bfs_profile")}
+        head = {k: result.pop(k) for k in list(result)
+                if k not in ("per_graph", "accuracy_vs_ground_truth", "bfs_profile")}
         out = dict(head)
         out.update(result)
         out.update(extra)

@@ -4,7 +4,8 @@ Picks the words per node W (64*W sources per tile), the team count and the
 top-down threshold alpha for a set of graphs by timing real launches of
 homln_batch_analyse on the GPU. The search is coordinate-wise: W first (teams
 and alpha at the library's defaults), then the team count at the best W, then
-alpha at the best (W, teams). Every candidate is timed ``reps`` times (at
+alpha at the best (W, teams), then whether the blocks that share an SM join the same team or
+different ones (team_mix). Every candidate is timed ``reps`` times (at
 least 3) and scored by its median. Results are cached per workload class
 (graph count, largest node count, total edges and degree skew, each bucketed
 to a power of two) in a JSON file under the build directory, so a serving
@@ -115,6 +116,7 @@ def tune(handles, masks, ns, edges, with_and=True, stream_ptr: int = 0, use_cach
     tcands = [t for t in teams if t == 0 or (t <= tiles and t * per_team <= STATE_LIMIT)]
     best = min((dict(best, teams=t) for t in tcands), key=run)
     best = min((dict(best, push_alpha=a) for a in alphas), key=run)
+    best = min((dict(best, team_mix=m) for m in (0, 1)), key=run)
     results.sort(key=lambda x: x[0])
     entry = {"tuning": best, "key": key, "reps": reps,
              "candidates": [{"ms": round(ms, 3), **t} for ms, t in results]}

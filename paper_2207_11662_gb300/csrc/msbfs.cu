@@ -126,9 +126,11 @@ constexpr uint8_t QUIET = 1;  // quiet byte of a full vertex
 
 __device__ __forceinline__ uint8_t level_mark(int level) { return (uint8_t)(1 + level % 255); }
 
-// Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices.
+// Vertices a warp takes from its team's work counter at a time, in passes of 32/T vertices (the
+// bottom-up group tier caps a chunk at 32 vertices). Measured on GB300 (4 BA layers, n = 200,000):
+// 8 passes, i.e. 32-vertex chunks at W = 16, 3% faster than 4.
 #ifndef HOMLN_CHUNK_PASSES
-#define HOMLN_CHUNK_PASSES 4
+#define HOMLN_CHUNK_PASSES 8
 #endif
 constexpr int kChunkPasses = HOMLN_CHUNK_PASSES;
 #ifndef HOMLN_WORDS_PER_LANE
