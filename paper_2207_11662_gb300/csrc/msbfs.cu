@@ -176,6 +176,22 @@ __device__ __forceinline__ void stw(uint64_t *p, const uint64_t (&x)[K]) {
     }
 }
 
+// Position of the k-th (0-based) set bit of m; k < popc(m). Chunk loops use it to hand the active
+// vertices of a 32-vertex chunk to the lane groups without gaps.
+__device__ __forceinline__ int nth_set(uint32_t m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 template <int T>
 __device__ __forceinline__ uint32_t group_sum(uint32_t v) {
 #pragma unroll
@@ -526,50 +542,66 @@ __device__ void phase_start_push(const Tile &a, uint64_t *fa, int32_t s0, int32_
 }
 
 // After a top-down level: of the words pushed into a vertex's words of the next snapshot (which
-// held state_{l-2}), the bits it did not have after the previous level are its new bits.
+// held state_{l-2}), the bits it did not have after the previous level are its new bits. Warps
+// sweep chunks of 32 consecutive vertices: one coalesced load of each per-vertex byte, then only
+// the vertices that were pushed to or found bits on the previous level are processed (a top-down
+// level has few). Every other live vertex has no new bits, keeps its words, and is not full (a
+// full one would have turned quiet): it only adds its edges to the unfinished count.
 template <int W, bool STATS>
 __device__ void phase_finalize(const Tile &a, const uint64_t *__restrict__ prv, uint64_t *nxt, int level, uint32_t ps,
                                PhaseCounters &c, unsigned long long *st) {
-    constexpr int K = Geo<W>::K, T = Geo<W>::T;
+    constexpr int K = Geo<W>::K, T = Geo<W>::T, per_pass = 32 / T;
     reset_next_slot(a, ps);
     const int lane = threadIdx.x & 31, q = lane % T;
-    const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
-    const int64_t G = ((int64_t)a.tsize * blockDim.x) / T;
+    const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
     const uint8_t last = level_mark(level - 1);
-    for (int64_t v = gtid / T; __any_sync(0xffffffffu, v < a.n); v += G) {
-        uint8_t qv = 0, pv = 0, fv = 0;
-        if (v < a.n) {
-            qv = a.quiet[v];
-            pv = a.pushed[v];
-            fv = a.fresh[v];
-            if (STATS && q == 0) st[ST_BYTES] += 3;
+    for (int64_t v0 = gw * 32; v0 < a.n; v0 += NW * 32) {  // uniform over the warp
+        const int cnt = (int)min((int64_t)32, (int64_t)a.n - v0);
+        const int64_t vl = v0 + lane;
+        int qv = QUIET, pv = 0, fv = 0;
+        if (lane < cnt) {
+            qv = a.quiet[vl];
+            pv = a.pushed[vl];
+            fv = a.fresh[vl];
+            if (STATS) st[ST_BYTES] += 3;
         }
-        const bool act = v < a.n && qv < QUIET;
-        const bool chg = fv == last;
-        uint64_t s[K], nw[K];
-        int64_t deg = 0;
+        const bool live = lane < cnt && qv < QUIET;
+        const int flags = (pv ? 1 : 0) | (fv == last ? 2 : 0);
+        const bool busy = live && flags != 0;
+        if (live && !busy) {
+            c.mu += (unsigned long long)(a.rowptr[vl + 1] - a.rowptr[vl]);
+            if (STATS) st[ST_BYTES] += 16;
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, busy);
+        const int nb = __popc(mask);
+        for (int pass = 0; pass * per_pass < nb; ++pass) {  // uniform over the warp
+            const int slot = pass * per_pass + lane / T;
+            const bool act = slot < nb;
+            const int src = act ? nth_set(mask, slot) : 0;
+            const int fl = __shfl_sync(0xffffffffu, flags, src);
+            const int64_t v = v0 + src;
+            const bool pushed = act && (fl & 1), chg = act && (fl & 2);
+            uint64_t s[K], nw[K];
+            int64_t deg = 0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) s[k] = nw[k] = 0;
-        if (act) {
-            deg = a.rowptr[v + 1] - a.rowptr[v];
-            if (STATS && q == 0) st[ST_BYTES] += 16;
-            // a vertex nobody pushed to has no new bits; its next words are current unless it
-            // found bits on the previous level (a non-quiet vertex whose words are full did)
-            if (pv || chg) {
+            for (int k = 0; k < K; ++k) s[k] = nw[k] = 0;
+            if (act) {
+                deg = a.rowptr[v + 1] - a.rowptr[v];
                 ldw<K>(prv + v * W + q * K, s);
-                if (STATS) st[ST_BYTES] += 8 * K;
-            }
-            if (pv) {
-                uint64_t z[K];
-                ldw<K>(nxt + v * W + q * K, z);
+                if (STATS) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
+                if (pushed) {
+                    uint64_t z[K];
+                    ldw<K>(nxt + v * W + q * K, z);
 #pragma unroll
-                for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
-                if (STATS) st[ST_BYTES] += 8 * K;
+                    for (int k = 0; k < K; ++k) nw[k] = z[k] & ~s[k];
+                    if (STATS) st[ST_BYTES] += 8 * K;
+                }
             }
+            commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, chg, c, st);
+            // after the group's shuffles in commit_vertex: every lane of the group has read the flags
+            if (pushed && q == 0) a.pushed[v] = 0;
         }
-        commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, deg, act && chg, c, st);
-        // after the group's shuffles in commit_vertex: every lane of the group has read pv
-        if (act && pv && q == 0) a.pushed[v] = 0;
     }
     flush_counters(a, c, ps);
 }
@@ -692,10 +724,10 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
     }
     // --- group tier: T lanes per vertex. Warps take chunks of consecutive vertices from the
     // team's work counter, so a slow vertex (no early exit, long row) delays only its own chunk.
-    // A chunk's row bounds and quiet bytes are read once, coalesced, and handed to the passes by
-    // shuffles; the warp's next chunk is reserved while the current one runs. A pass then waits
-    // for one load (seen words and the first column indices, issued together) before its
-    // frontier gathers, instead of three in a row.
+    // A chunk's row bounds and quiet and fresh bytes are read once, coalesced, and only its live
+    // (non-quiet) vertices go to the passes, by shuffles; the warp's next chunk is reserved while
+    // the current one runs. A pass then waits for one load (the vertex's words and its first
+    // column indices, issued together) before its gathers, instead of three in a row.
     {
         unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
         constexpr int per_pass = 32 / T;
@@ -709,21 +741,24 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
             if (lane == 0) next = (long long)atomicAdd(work, (unsigned long long)chunk);
             const int64_t v0 = a.hub_warp_end + base;
             const int cnt = (int)min((int64_t)chunk, (int64_t)(nrest - base));  // vertices of this chunk
-            // lane i holds vertex v0+i's row bounds and quiet byte (i < cnt)
+            // lane i holds vertex v0+i's row bounds and its quiet and fresh bytes (i < cnt)
             const int64_t rb_l = a.prow[v0 + min(lane, cnt)];
             const int64_t re_l = a.prow[v0 + min(lane + 1, cnt)];
             // quiet byte | fresh byte << 8 of vertex v0+lane
             const int qf_l = lane < cnt ? (int)a.quiet[v0 + lane] | ((int)a.fresh[v0 + lane] << 8) : (int)QUIET;
-            for (int pass = 0; pass * per_pass < cnt; ++pass) {  // uniform over the warp
-                const int i = pass * per_pass + lane / T;
+            if (STATS && lane < cnt) st[ST_BYTES] += 2;
+            // the chunk's live (non-quiet) vertices, handed to the lane groups without gaps
+            const uint32_t live = __ballot_sync(0xffffffffu, lane < cnt && (qf_l & 0xff) < QUIET);
+            const int nl = __popc(live);
+            for (int pass = 0; pass * per_pass < nl; ++pass) {  // uniform over the warp
+                const int slot = pass * per_pass + lane / T;
+                const bool act = slot < nl;
+                const int i = act ? nth_set(live, slot) : 0;
                 const int64_t v = v0 + i;
-                const int qf = __shfl_sync(0xffffffffu, qf_l, i & 31);
-                const int qv = qf & 0xff;
-                const bool chg = (qf >> 8) == (int)last;
-                const int64_t rb0 = __shfl_sync(0xffffffffu, (long long)rb_l, i & 31);
-                const int64_t re0 = __shfl_sync(0xffffffffu, (long long)re_l, i & 31);
-                if (STATS && q == 0 && i < cnt) st[ST_BYTES] += 2;
-                const bool act = i < cnt && qv < QUIET;
+                const int qf = __shfl_sync(0xffffffffu, qf_l, i);
+                const bool chg = act && (qf >> 8) == (int)last;
+                const int64_t rb0 = __shfl_sync(0xffffffffu, (long long)rb_l, i);
+                const int64_t re0 = __shfl_sync(0xffffffffu, (long long)re_l, i);
                 uint64_t s[K], need[K], acc[K], nw[K];
                 int32_t u[kUnroll];
                 bool lane_need = false;
@@ -752,7 +787,7 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 }
 #pragma unroll
                 for (int k = 0; k < K; ++k) nw[k] = acc[k] & need[k];
-                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, act && chg, c, st);
+                commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, chg, c, st);
             }
         }
     }
@@ -768,8 +803,8 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint
     constexpr int K = Geo<W>::K, T = Geo<W>::T;
     const int lane = threadIdx.x & 31;
     const int q = lane % T;
-    auto push_row = [&](int64_t v, int p, int S) {
-        if (a.fresh[v] != level_mark(level - 1)) return;  // no new bits on the previous level
+    auto push_row = [&](int64_t v, int p, int S, bool known) {
+        if (!known && a.fresh[v] != level_mark(level - 1)) return;  // no new bits on the previous level
         uint64_t f[K];
         ldw<K>(cur + v * W + q * K, f);
         if (STATS) st[ST_BYTES] += 8 * K + 1;
@@ -792,22 +827,32 @@ __device__ void phase_push(const Tile &a, const uint64_t *__restrict__ cur, uint
             if (STATS) st[ST_BYTES] += 1;
         }
     };
-    for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) push_row(v, threadIdx.x / T, blockDim.x / T);
+    for (int64_t v = a.rank; v < a.hub_block_end; v += a.tsize) push_row(v, threadIdx.x / T, blockDim.x / T, false);
     const int64_t gw = ((int64_t)a.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t NW = ((int64_t)a.tsize * blockDim.x) >> 5;
-    for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) push_row(v, lane / T, 32 / T);
-    // group tier: chunks from the team's work counter (this phase's slot, cleared beforehand)
+    for (int64_t v = a.hub_block_end + gw; v < a.hub_warp_end; v += NW) push_row(v, lane / T, 32 / T, false);
+    // group tier: chunks of 32 consecutive vertices from the team's work counter (this phase's slot,
+    // cleared beforehand); one coalesced load of their fresh bytes finds the chunk's pushers, which
+    // the lane groups then take without gaps
     unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
-    const int64_t per_pass = 32 / T;
-    const int64_t chunk = per_pass * kChunkPasses;
+    constexpr int per_pass = 32 / T;
     const int64_t nrest = a.n - a.hub_warp_end;
+    const uint8_t last = level_mark(level - 1);
     for (;;) {
         long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd(work, (unsigned long long)chunk);
+        if (lane == 0) base = (long long)atomicAdd(work, 32ull);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nrest) break;
-        const int64_t vend = a.hub_warp_end + min((int64_t)base + chunk, nrest);
-        for (int64_t v = a.hub_warp_end + base + lane / T; v < vend; v += per_pass) push_row(v, 0, 1);
+        if (base >= nrest) break;  // uniform over the warp
+        const int64_t v0 = a.hub_warp_end + base;
+        const int cnt = (int)min((int64_t)32, (int64_t)(nrest - base));
+        const bool pusher = lane < cnt && a.fresh[v0 + lane] == last;
+        if (STATS && lane < cnt) st[ST_BYTES] += 1;
+        const uint32_t mask = __ballot_sync(0xffffffffu, pusher);
+        const int np = __popc(mask);
+        for (int pass = 0; pass * per_pass < np; ++pass) {
+            const int slot = pass * per_pass + lane / T;
+            if (slot < np) push_row(v0 + nth_set(mask, slot), 0, 1, true);
+        }
     }
 }
 
