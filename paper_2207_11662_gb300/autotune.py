@@ -2,8 +2,8 @@
 
 Picks the words per node W (64*W sources per tile), the team count and the
 top-down threshold alpha for a set of graphs by timing real launches of
-homln_batch_analyse on the GPU. The search is coordinate-wise: W first (teams
-and alpha at the library's defaults), then the team count at the best W, then
+homln_batch_analyse on the GPU. The search is coordinate-wise: W first (at two
+values of alpha, teams at the library's default), then the team count at the best W, then
 alpha at the best (W, teams), then whether the blocks that share an SM join the same team or
 different ones (team_mix). Every candidate is timed ``reps`` times (at
 least 3) and scored by its median. Results are cached per workload class
@@ -110,7 +110,8 @@ def tune(handles, masks, ns, edges, with_and=True, stream_ptr: int = 0, use_cach
 
     # W: no wider than the node count needs, one team's state within the limit
     ws = [w for w in words if 64 * (w // 2) < maxn and 2.0 * maxn * 8.0 * w <= STATE_LIMIT] or [1]
-    best = min(({"words_per_node": w, "teams": 0, "push_alpha": 16} for w in ws), key=run)
+    # W together with two direction thresholds: a wide tile can win only with more top-down levels
+    best = min(({"words_per_node": w, "teams": 0, "push_alpha": a} for w in ws for a in (4, 16)), key=run)
     tiles = sum(-(-n // (64 * best["words_per_node"])) for n in ns)
     per_team = 2.0 * maxn * 8.0 * best["words_per_node"]
     tcands = [t for t in teams if t == 0 or (t <= tiles and t * per_team <= STATE_LIMIT)]
