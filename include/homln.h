@@ -347,7 +347,8 @@ typedef struct homln_profile_t {
  * several requests share one GPU). A yield flag is one int32 in pinned host memory that the GPU
  * reads directly.
  *   homln_yield_create   allocate a flag, lowered (0). Errors: EINVAL (out NULL), ECUDA.
- *   homln_yield_destroy  free it; no handle may still watch it (NULL is accepted).
+ *   homln_yield_destroy  free it (NULL is accepted). Errors: EBUSY while a handle still watches it;
+ *                        homln_set_yield(h, NULL) or homln_destroy(h) ends the watching.
  *   homln_yield_set      raise (nonzero) or lower (0) the flag; callable from any host thread.
  *   homln_yield_count    how many times BFS launches watching the flag stopped early for it.
  *   homln_set_yield      the persistent BFS of calls led by handle h (its analyses, and batches

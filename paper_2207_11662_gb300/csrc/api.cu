@@ -147,6 +147,8 @@ struct Lanes {
 
 struct homln_graph_s;
 
+struct homln_yield_s;
+
 struct homln_s {
     Lanes lanes;
     Alloc al;  // declared before the buffers: destroyed after every buffer that uses it
@@ -164,6 +166,7 @@ struct homln_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     long long bfs_launches = 0;
     int live_graphs = 0;  // captured graphs that involve this handle
+    homln_yield_s *yield = nullptr;  // the yield flag this handle's BFS watches (homln_set_yield)
     BfsStats stats;
     ~homln_s() {
         for (auto &e : events) {
@@ -629,6 +632,7 @@ struct homln_yield_s {
     int32_t *host = nullptr;
     int32_t *dev = nullptr;
     std::atomic<long long> count{0};
+    std::atomic<int> watchers{0};  // handles whose BFS watches this flag
     ~homln_yield_s() {
         if (host) cudaFreeHost(host);
     }
@@ -651,6 +655,8 @@ homln_status homln_yield_create(homln_yield_t *out) {
 
 homln_status homln_yield_destroy(homln_yield_t y) {
     API_BEGIN
+    if (y && y->watchers.load() > 0)
+        fail(HOMLN_EBUSY, "a handle still watches this yield flag (homln_set_yield(h, NULL) or destroy it first)");
     delete y;
     API_END
 }
@@ -673,6 +679,9 @@ homln_status homln_set_yield(homln_t h, homln_yield_t y) {
     API_BEGIN
     if (!h) fail(HOMLN_EINVAL, "handle is NULL");
     if (h->live_graphs > 0) fail(HOMLN_EBUSY, "a captured graph uses this handle");
+    if (h->yield) h->yield->watchers.fetch_sub(1);
+    h->yield = y;
+    if (y) y->watchers.fetch_add(1);
     h->tuning.yield_host = y ? y->host : nullptr;
     h->tuning.yield_dev = y ? y->dev : nullptr;
     h->tuning.yield_count = y ? &y->count : nullptr;
@@ -740,6 +749,7 @@ homln_status homln_destroy(homln_t h) {
     if (!h) return HOMLN_OK;
     API_BEGIN
     if (h->live_graphs > 0) fail(HOMLN_EBUSY, "a captured graph still uses this handle; destroy it first");
+    homln_set_yield(h, nullptr);  // stop watching a yield flag, so that the flag can be destroyed
     cudaSetDevice(h->device);
     cudaStream_t s = h->stream;
     // buffers owned by a lane are freed on it: after everything queued on the handle's stream

@@ -112,3 +112,13 @@ int main() {
     subprocess.check_call([gxx, "-std=c++17", "-I", inc, "-I", os.path.join(ROOT, "paper_2207_11662_gb300", "csrc"),
                            str(src), "-o", str(exe)])
     assert subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip() == "0"
+
+
+def test_yield_flag_arguments_without_gpu(H):
+    """The yield-flag calls reject NULL arguments on the host, before touching a GPU."""
+    import ctypes
+    assert H.lib.homln_yield_set(None, 1) == H.HOMLN_EINVAL
+    assert H.lib.homln_yield_count(None, ctypes.byref(ctypes.c_int64())) == H.HOMLN_EINVAL
+    assert H.lib.homln_set_yield(None, None) == H.HOMLN_EINVAL
+    assert H.lib.homln_yield_create(None) == H.HOMLN_EINVAL
+    assert H.lib.homln_yield_destroy(None) == H.HOMLN_OK

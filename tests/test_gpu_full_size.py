@@ -220,7 +220,13 @@ def test_yield_flag_stops_and_resumes_the_bfs(H, golden):
         with pytest.raises(H.HomlnError) as err:  # a watching handle cannot be captured
             H.homln_graph_capture([g.h], [(1 << net.n_layers) - 1], True)
         assert err.value.code == H.HOMLN_EINVAL
+        with pytest.raises(H.HomlnError) as err:  # nor can the flag be freed while watched
+            H.homln_yield_destroy(y)
+        assert err.value.code == H.HOMLN_EBUSY
         H.homln_set_yield(g.h, None)
+        h2 = H.homln_create(net.n, to_dev(net.layers[:1]))  # destroying a watching handle ends its watch
+        H.homln_set_yield(h2, y)
+        H.homln_destroy(h2)
     finally:
         g.close()
         H.homln_yield_destroy(y)
