@@ -490,33 +490,43 @@ __device__ __forceinline__ void commit_vertex(const Tile &a, bool act, bool writ
 template <int W, bool STATS>
 __device__ void phase_start_batch(const Tile &a, uint64_t *s0buf, uint64_t *s1buf, int32_t s0, int32_t ns,
                                   unsigned long long *st) {
+    constexpr int V = W >= 2 ? 2 : 1;  // words per store: 16-byte stores where a node has 2 or more
     const int64_t nthreads = (int64_t)a.tsize * blockDim.x;
     const int64_t gtid = (int64_t)a.rank * blockDim.x + threadIdx.x;
     // the batch's sources below the split are bits 0 .. split-1, the rest split .. ns-1
     const int32_t split = min(max(a.gend - s0, 0), ns);
-    for (int64_t i = gtid; i < (int64_t)a.n * W; i += nthreads) {
+    for (int64_t i = gtid * V; i < (int64_t)a.n * W; i += nthreads * V) {
         const int64_t v = i / W;
-        const int wi = (int)(i % W);
-        const int lo = wi * 64;
+        const int wi0 = (int)(i % W);
         // bits c0 .. c1-1 of the batch can reach v; the rest are set
         const int32_t c0 = v < a.gend ? 0 : split, c1 = v < a.gend ? split : ns;
-        const int32_t b0 = max(c0 - lo, 0), b1 = min(c1 - lo, 64);
-        uint64_t x = ~0ull;
-        if (b1 > b0) x = ~((b1 - b0 == 64 ? ~0ull : ((1ull << (b1 - b0)) - 1)) << b0);
         const bool source = v >= s0 && v < (int64_t)s0 + ns;
-        if (source) {
-            const int b = (int)(v - s0);
-            if ((b >> 6) == wi) x |= 1ull << (b & 63);
+        uint64_t x[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int wi = wi0 + k, lo = wi * 64;
+            const int32_t b0 = max(c0 - lo, 0), b1 = min(c1 - lo, 64);
+            x[k] = ~0ull;
+            if (b1 > b0) x[k] = ~((b1 - b0 == 64 ? ~0ull : ((1ull << (b1 - b0)) - 1)) << b0);
+            if (source) {
+                const int b = (int)(v - s0);
+                if ((b >> 6) == wi) x[k] |= 1ull << (b & 63);
+            }
         }
-        s0buf[i] = x;  // both snapshots hold state_0
-        s1buf[i] = x;
-        if (wi == 0) {
+        if constexpr (V == 2) {  // both snapshots hold state_0
+            *reinterpret_cast<ulonglong2 *>(s0buf + i) = make_ulonglong2(x[0], x[1]);
+            *reinterpret_cast<ulonglong2 *>(s1buf + i) = make_ulonglong2(x[0], x[1]);
+        } else {
+            s0buf[i] = x[0];
+            s1buf[i] = x[0];
+        }
+        if (wi0 == 0) {
             const bool lonely = c1 - c0 - (source ? 1 : 0) <= 0 || a.prow[v + 1] == a.prow[v];
             a.quiet[v] = lonely ? QUIET : 0;
             a.fresh[v] = 0;
             a.pushed[v] = 0;
         }
-        if (STATS) st[ST_BYTES] += 16 + (wi == 0 ? 3 + 16 : 0);
+        if (STATS) st[ST_BYTES] += 16 * V + (wi0 == 0 ? 3 + 16 : 0);
     }
 }
 
