@@ -369,7 +369,8 @@ def roofline(workload, m, hp_tuning):
 
 def per_graph_teps(H, net, dev, stream, tuning, per_graph_work, reps=3):
     """Each layer's and the AND graph's all-sources BFS in a launch of its own (a fresh handle each,
-    best of reps), CUDA-event timed around the launch: GTEPS per graph."""
+    best of reps), CUDA-event timed around the launch: GTEPS per graph; and the ground truth as one
+    call (AND aggregation, relabelling, BFS and closeness of the AND graph), timed around the call."""
     import torch
     n, L = net.n, net.n_layers
     layers = [(torch.from_numpy(s).to(dev), torch.from_numpy(d).to(dev)) for s, d in net.layers]
@@ -393,6 +394,24 @@ def per_graph_teps(H, net, dev, stream, tuning, per_graph_work, reps=3):
                 H.homln_destroy(h)
         out.append({"graph": f"layer {g}" if g < L else "AND", "bfs_ms": round(best, 3),
                     "gteps": round(per_graph_work[g] / best / 1e6, 1)})
+    # the ground truth as one call: AND aggregation of the layers' CSRs, relabelling, BFS, closeness
+    best = float("inf")
+    for _ in range(reps):
+        h = H.homln_create(n, layers, stream=stream.cuda_stream)
+        try:
+            if tuning:
+                H.homln_set_tuning(h, **tuning)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.homln_and_closeness(h, (1 << L) - 1, F, None, None)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        finally:
+            H.homln_destroy(h)
+    out[-1]["ground_truth_call_ms"] = round(best, 3)
+    out[-1]["ground_truth_gteps"] = round(per_graph_work[L] / best / 1e6, 1)
     return out
 
 
