@@ -883,7 +883,12 @@ __device__ bool run_batch(const Tile &a, uint64_t *sa, uint64_t *sb, const TeamB
     for (int level = 2; level <= a.n + 1; ++level) {
         const unsigned long long *slot = a.ctr + 4 * ((ps - 1) % 3);
         const unsigned long long newbits = __ldcg(slot), mf = __ldcg(slot + 1), mu = __ldcg(slot + 2);
-        if (newbits == 0) break;
+        // done when the last level found nothing, or (undirected) when every vertex that can still
+        // change is full: no unfinished edges, and a vertex without edges gets no bits. Later levels
+        // would add no bit, and the snapshots need not be brought level once the batch ends. (A
+        // directed level counts unfinished edges by out-degree after a top-down level, which says
+        // nothing about in-edges.)
+        if (newbits == 0 || (mu == 0 && a.prow == a.rowptr)) break;
         const bool push = (unsigned long long)a.push_alpha * mf < mu;
         if (push) {
             phase_push<W, STATS>(a, cur, nxt, level, ps, st);
@@ -1365,7 +1370,7 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
                     unsigned long long h3[3];
                     HCUDA(cudaMemcpyAsync(h3, p->ctr.p + 4 * ((ps - 1) % 3), sizeof(h3), cudaMemcpyDeviceToHost, s));
                     HCUDA(cudaStreamSynchronize(s));
-                    if (h3[0] == 0) break;
+                    if (h3[0] == 0 || (h3[2] == 0 && !p->jobs[gi].g->directed)) break;
                     if ((unsigned long long)A.push_alpha * h3[1] < h3[2]) {
                         launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_PUSH, s0, ns, level, ps, cur_a);
                         launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, level, ps,

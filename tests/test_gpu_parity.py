@@ -224,6 +224,27 @@ def test_batch_analyse_mixes_directed_and_undirected(H):
         g.close()
 
 
+def test_directed_sinks_reached_after_the_core_is_full(H):
+    """A strongly connected core (0..199) with sinks (200..299, out-degree 0) hanging off it, every
+    level top-down, 64 sources per batch and no relabelling: in the batches whose sources all lie
+    in the core, the core vertices become full while the sinks still wait for their last bits one
+    level later. The BFS must run that level (nothing may end a directed batch early because the
+    vertices that are not full have no out-edges)."""
+    rng = np.random.default_rng(17)
+    core = 200
+    s = list(range(core)) + list(rng.integers(0, core, 400))
+    d = [(i + 1) % core for i in range(core)] + list(rng.integers(0, core, 400))
+    for k in range(100):  # sink 200 + k, fed by one or two core vertices
+        for _ in range(1 + k % 2):
+            s.append(int(rng.integers(0, core)))
+            d.append(core + k)
+    net = synth.HoMLN(300, [(np.array(s, np.int32), np.array(d, np.int32))])
+    sel = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0), O.Select(O.TOPK_PERCENT, 10.0))]
+    for alpha in (1000000, 16):
+        full_parity(H, net, sel, tuning=dict(words_per_node=1, push_alpha=alpha, relabel=0), heuristics=(2,),
+                    directed=True)
+
+
 def test_directed_or_hubs_and_closed_forms(H):
     """Directed OR graphs, an in-star and an out-star (hub tiers on the in-CSR), a directed path and cycle."""
     n = 3000
