@@ -117,10 +117,12 @@ def sels_of(H):
             "ge_mean": H.make_select(H.HOMLN_GE_MEAN, cc1_overlap=0.5)}
 
 
-@pytest.mark.parametrize("tuning", [None, dict(words_per_node=16, teams=8, push_alpha=4)])
+@pytest.mark.parametrize("tuning", [None, dict(words_per_node=16, teams=8, push_alpha=4),
+                                    dict(words_per_node=8, teams=32, push_alpha=16, team_mix=1)])
 def test_powerlaw_full_size_matches_oracle(H, golden, tuning):
     """4 Chung-Lu layers on 50,000 nodes: every output against the oracle's full run, in the library's
-    default launch configuration and in another (wider tiles, fewer teams, another direction switch);
+    default launch configuration, in the setting the benchmark's autotuner picks (32 teams, blocks of an
+    SM in different teams) and in another (wider tiles, fewer teams, another direction switch);
     F/R/closeness also against a live oracle BFS from 2,000 seeded sources."""
     net = synth.homln_powerlaw()
     ent = golden["powerlaw50k"]
@@ -133,11 +135,13 @@ def test_powerlaw_full_size_matches_oracle(H, golden, tuning):
     g.close()
 
 
-@pytest.mark.parametrize("tuning", [None, dict(words_per_node=4, teams=32, push_alpha=64)])
+@pytest.mark.parametrize("tuning", [None, dict(words_per_node=16, teams=16, push_alpha=4, team_mix=1),
+                                    dict(words_per_node=4, teams=32, push_alpha=64)])
 def test_large_ba_full_size_matches_oracle(H, golden, tuning):
     """4 Barabasi-Albert layers on 200,000 nodes (~50% shared edges): every output against the oracle's
-    full run (all 200,000 sources of all 5 graphs), in two launch configurations; F/R/closeness also
-    against a live oracle BFS from 2,000 seeded sources."""
+    full run (all 200,000 sources of all 5 graphs), in the library's defaults, in the setting the
+    benchmark's autotuner picks (1,024 sources per tile, alpha 4, blocks of an SM in different teams)
+    and in a third; F/R/closeness also against a live oracle BFS from 2,000 seeded sources."""
     net = synth.homln_ba_large()
     ent = golden["ba200k"]
     check_inputs(net, ent)
