@@ -2,10 +2,13 @@
 
 Each translation unit in ``csrc/`` is compiled in parallel into ``_build/``,
 then linked into ``paper_2207_11662_gb300/libhomln.so``. A unit is rebuilt only
-when it or a header is newer than its object file.
+when it or a header is newer than its object file. Processes that build at the same
+time (test workers, spawned pools) take turns on a lock file in ``_build/``: the first
+compiles, the others then find everything up to date.
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -43,6 +46,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     compile-time knobs -DHOMLN_GATHER_UNROLL=8 or -DHOMLN_BFS_MIN_BLOCKS=3; a change of
     these flags rebuilds everything."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)  # released when the file is closed
+        return _build_locked(force, verbose)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     nvcc = _nvcc()
     extra = os.environ.get("HOMLN_NVCC_EXTRA", "").split()
     stamp = os.path.join(BUILD, "flags.txt")
@@ -63,11 +72,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         src, obj, stale = job
         if not stale:
             return None
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+        tmp = obj + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             return f"{' '.join(cmd)}\n{r.stdout}\n{r.stderr}"
-        os.replace(obj + ".tmp", obj)
+        os.replace(tmp, obj)
         if verbose:
             print(r.stderr)
         return None

@@ -122,3 +122,23 @@ def test_yield_flag_arguments_without_gpu(H):
     assert H.lib.homln_set_yield(None, None) == H.HOMLN_EINVAL
     assert H.lib.homln_yield_create(None) == H.HOMLN_EINVAL
     assert H.lib.homln_yield_destroy(None) == H.HOMLN_OK
+
+
+def test_concurrent_builds_take_turns(H):
+    """A second process that builds while the build lock is held waits for it, then finds the
+    library up to date; per-process temporary names keep two compilers off one file."""
+    import fcntl
+    import subprocess
+    import sys
+    import time
+    from paper_2207_11662_gb300 import build_ext
+    before = os.path.getmtime(build_ext.LIB)
+    code = "import sys; sys.path.insert(0, %r); from paper_2207_11662_gb300 import build_ext; build_ext.build()" % ROOT
+    with open(os.path.join(build_ext.BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        child = subprocess.Popen([sys.executable, "-c", code])
+        time.sleep(2.0)
+        assert child.poll() is None, "the second build did not wait for the lock"
+    assert child.wait(timeout=300) == 0
+    assert os.path.getmtime(build_ext.LIB) == before  # nothing was stale: no relink
+    assert not [f for f in os.listdir(build_ext.BUILD) if ".tmp" in f]
