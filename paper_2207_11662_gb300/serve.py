@@ -24,13 +24,22 @@ Scheduling:
     remaining tiles when the flag is lowered. So a small request that arrives while a big
     one is on the GPU waits about one BFS tile, not the whole big request. (``small_sms``
     instead splits the GPU by SMs between the two kinds of waves, without preemption;
-    measured slower.) With one worker every wave takes the whole GPU, in arrival order.
+    measured slower.) With one worker every wave takes the whole GPU, in arrival order;
+  * no collector pauses: Python's full (oldest-generation) cyclic garbage collection
+    walks every tracked object of the process while holding the interpreter lock; with
+    torch loaded that is ~10^5 objects and tens of ms, during which no worker thread can
+    launch or collect a wave. ``freeze_gc`` (default on) moves the objects that exist
+    when ``run`` starts out of the collector's view for the run (``gc.freeze``) and
+    gives them back afterwards (``gc.unfreeze``, which also undoes a freeze the process
+    made before), so a collection during the run only walks what the run itself created.
 
 Every GPU step runs in libhomln.so; this module only schedules.
 """
 from __future__ import annotations
 
 import collections
+import contextlib
+import gc
 import threading
 import time
 from dataclasses import dataclass, field
@@ -150,6 +159,21 @@ class Admission:
             self.cv.notify_all()
 
 
+@contextlib.contextmanager
+def gc_frozen(enabled: bool = True):
+    """Keep the objects that exist on entry out of the cyclic collector until exit (gc.freeze);
+    on exit every frozen object goes back to the oldest generation (gc.unfreeze), including any
+    the process had frozen before entry."""
+    if not enabled:
+        yield
+        return
+    gc.freeze()
+    try:
+        yield
+    finally:
+        gc.unfreeze()
+
+
 def work_estimate(n: int, edge_counts) -> int:
     """BFS work of a request, nodes x edges over its layers (a bound on its edge visits / 2)."""
     return int(n) * int(sum(edge_counts))
@@ -158,7 +182,8 @@ def work_estimate(n: int, edge_counts) -> int:
 class Server:
     def __init__(self, device: int = 0, workers: int = 2, max_wave: int = 16, mem_budget_bytes: int = 16 << 30,
                  percent: float = 10.0, keep_farness: bool = False, tuning: dict | None = None,
-                 big_work: float = 2e10, preempt: bool = True, small_sms: int = 0, big_max_tiles: int = 0):
+                 big_work: float = 2e10, preempt: bool = True, small_sms: int = 0, big_max_tiles: int = 0,
+                 freeze_gc: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -169,6 +194,7 @@ class Server:
         self.small_sms = max(0, min(int(small_sms), self.nsm - 1))
         self.preempt = bool(preempt) and workers >= 2 and self.small_sms == 0
         self.big_max_tiles = big_max_tiles
+        self.freeze_gc = bool(freeze_gc)
         self._yield = None          # the yield flag big waves watch (preempt)
         self._small_active = 0      # small waves running; the flag is raised while > 0
         self._ylock = threading.Lock()
@@ -279,6 +305,10 @@ class Server:
 
     def run(self, requests, realtime: bool = True):
         """Replay the requests at their arrival times (or all at once) and serve them; returns them done."""
+        with gc_frozen(self.freeze_gc):
+            return self._run(requests, realtime)
+
+    def _run(self, requests, realtime: bool):
         self.t0 = time.perf_counter()
         self.done = []
         if self.preempt:

@@ -97,3 +97,26 @@ def test_single_worker_takes_the_oldest_class_first():
         a.submit(r, 10, cls)
     assert [r.rid for r, _ in a.take(8, 0.01)] == [1]  # the big request arrived first
     assert [r.rid for r, _ in a.take(8, 0.01)] == [0, 2]
+
+
+def test_gc_frozen_hides_old_objects_from_the_collector_and_restores():
+    """Inside the block a full collection walks only what the block created, and cyclic garbage
+    made inside is still collected; on exit every frozen object is back in the collector's view."""
+    import gc
+    serve = _mods()
+    before = len(gc.get_objects())
+    with serve.gc_frozen():
+        assert gc.get_freeze_count() >= before * 0.9
+        assert len(gc.get_objects()) < before * 0.1
+        cycle = []
+        cycle.append(cycle)
+        del cycle
+        assert gc.collect() >= 1
+    assert gc.get_freeze_count() == 0
+    assert len(gc.get_objects()) >= before * 0.9
+    gc.freeze()
+    try:
+        with serve.gc_frozen(False):
+            assert gc.get_freeze_count() > 0  # disabled: the collector's state is left alone
+    finally:
+        gc.unfreeze()
