@@ -292,27 +292,6 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b) {
 #define HOMLN_BLOCK_TIER_ITERS 4
 #endif
 constexpr int kUnroll = HOMLN_GATHER_UNROLL;
-// HOMLN_ASYNC_GATHER=1: the bottom-up group tier lands its neighbours' words in a per-thread
-// ring of shared memory with asynchronous 16-byte copies (cp.async), two batches of kUnroll
-// neighbours in flight instead of one batch held in registers.
-#ifndef HOMLN_ASYNC_GATHER
-#define HOMLN_ASYNC_GATHER 0
-#endif
-constexpr int kRingStages = 2;
-// dynamic shared memory of the BFS kernels: the ring (16 bytes per thread, stage and neighbour)
-inline size_t ring_bytes(int threads) {
-    return HOMLN_ASYNC_GATHER ? (size_t)kRingStages * kUnroll * (size_t)threads * 16 : 0;
-}
-
-#if HOMLN_ASYNC_GATHER
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-#endif
 
 #ifndef HOMLN_DEBUG
 #define HOMLN_DEBUG 0
@@ -372,64 +351,6 @@ __device__ __forceinline__ int64_t gather_or(const Tile &a, const uint64_t *__re
         j = jn;
     }
 }
-
-#if HOMLN_ASYNC_GATHER
-// gather_or with the neighbours' words landing in shared memory (group tier, S = 1, K = 2). The
-// thread's ring holds kRingStages batches of kUnroll 16-byte slots; g counts the copy groups this
-// thread has committed (batch g uses stage g mod kRingStages) and carries over from vertex to
-// vertex. Before a batch is issued, every group but the newest has landed, so the stage's
-// previous batch is no longer written; a batch is read once it has landed. The batch after the
-// current one is issued before the current one is read: two batches in flight. On early exit
-// the prefetched batch is left to land unread. rows counts the words copied (neighbours).
-template <int W>
-__device__ __forceinline__ int64_t gather_or_ring(const Tile &a, const uint64_t *__restrict__ cur, int64_t rb,
-                                                  int64_t re, int q, int32_t (&u)[kUnroll],
-                                                  const uint64_t (&need)[Geo<W>::K], uint64_t (&acc)[Geo<W>::K],
-                                                  uint4 *ring, uint32_t &g, int64_t &rows) {
-    constexpr int K = Geo<W>::K, U = kUnroll;
-    static_assert(K == 2, "the ring holds 16-byte lane parts");
-    int64_t j = rb;
-    if (j >= re) return 0;
-    const int nt = blockDim.x;
-    uint4 *mine = ring + threadIdx.x;
-    auto issue = [&](uint32_t grp) {
-        cp_async_wait<1>();
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const bool ok = u[i] >= 0 && id_ok(a, u[i]);
-            const uint64_t *src = ok ? cur + (int64_t)u[i] * W + q * K : cur;
-            cp_async16(mine + (size_t)((grp % kRingStages) * U + i) * nt, src, ok);
-            rows += ok;
-        }
-        cp_async_commit();
-    };
-    uint32_t cg = g;
-    issue(g++);
-    int64_t it = 0;
-    while (true) {
-        const int64_t jn = j + U;
-        const bool more = jn < re;
-        const int64_t here = min(re, jn) - j;
-        if (more) {
-            load_cols(a, jn, re, 1, u);
-            issue(g++);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const uint4 x = mine[(size_t)((cg % kRingStages) * U + i) * nt];
-            acc[0] |= ((uint64_t)x.y << 32) | x.x;
-            acc[1] |= ((uint64_t)x.w << 32) | x.z;
-        }
-        it += here;
-        if (!more || covers<K>(acc, need)) return it;
-        ++cg;
-        j = jn;
-    }
-}
-#endif
 
 // The warp-tier gather: the 32/T slots of one warp take every (32/T)-th neighbour of the
 // same row; after each step their partial results are OR-ed across the warp, so all slots
@@ -819,10 +740,6 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
     // column indices, issued together) before its gathers, instead of three in a row.
     {
         unsigned long long *work = a.ctr + 4 * (ps % 3) + 3;
-#if HOMLN_ASYNC_GATHER
-        extern __shared__ uint4 s_ring[];
-        uint32_t ring_g = 0;  // copy groups committed by this thread (none pending between phases)
-#endif
         constexpr int per_pass = 32 / T;
         constexpr int chunk = per_pass * kChunkPasses < 32 ? per_pass * kChunkPasses : 32;
         const int64_t nrest = a.n - a.hub_warp_end;
@@ -869,21 +786,11 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                         lane_need |= need[k] != 0;
                     }
                 }
-                int64_t it = 0, rw = 0;  // neighbours visited; words loaded (neighbours)
-#if HOMLN_ASYNC_GATHER
-                if constexpr (K == 2) {
-                    if (lane_need) it = gather_or_ring<W>(a, cur, rb, re, q, u, need, acc, s_ring, ring_g, rw);
-                } else {
-                    if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, u, need, acc);
-                    rw = it;
-                }
-#else
+                int64_t it = 0;
                 if (lane_need) it = gather_or<W>(a, cur, rb, re, 0, 1, q, u, need, acc);
-                rw = it;
-#endif
                 if (STATS) {
-                    st[ST_WORDS] += rw * K;
-                    st[ST_BYTES] += rw * 8 * K;
+                    st[ST_WORDS] += it * K;
+                    st[ST_BYTES] += it * 8 * K;
                     int64_t gm = group_max<T>(it);
                     if (q == 0) { st[ST_EDGES] += gm; st[ST_BYTES] += 4 * gm; }
                     if (act) st[ST_BYTES] += 8 * K + (q == 0 ? 16 : 0);
@@ -893,9 +800,6 @@ __device__ void phase_pull(const Tile &a, const uint64_t *__restrict__ cur, uint
                 commit_vertex<W, STATS>(a, act, true, v, q, s, nw, nxt, level, re - rb, chg, c, st);
             }
         }
-#if HOMLN_ASYNC_GATHER
-        cp_async_wait<0>();  // prefetches left after early exits land before the ring is reused
-#endif
     }
     flush_counters(a, c, ps);
 }
@@ -1248,7 +1152,6 @@ struct BfsPlan {
     BfsTuning t;
     bool plain = false, stats = false;
     int W = 8, nteams = 1, threads = 512, grid = 0, nsm = 0, per_sm = 0;
-    size_t smem = 0;  // dynamic shared memory of the BFS kernels
     BfsKernel kern = nullptr;
     PhaseKernel pkern = nullptr;
     std::vector<GraphDesc> desc;
@@ -1306,14 +1209,7 @@ BfsPlan *bfs_plan_create(const std::vector<BfsJob> &jobs, const BfsTuning &t, in
     HCUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) fail(HOMLN_ECUDA, "device does not support cooperative launch");
     p->pkern = plain ? phase_kernel_for(W, stats) : nullptr;
-    p->smem = ring_bytes(threads);
-    if (p->smem > 0) {
-        HCUDA(cudaFuncSetAttribute((const void *)p->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
-        if (p->pkern)
-            HCUDA(cudaFuncSetAttribute((const void *)p->pkern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)p->smem));
-    }
-    HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, threads, p->smem));
+    HCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern, threads, 0));
     if (per_sm < 1) fail(HOMLN_ECUDA, "bfs kernel does not fit on an SM");
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
     // sm_count: a grid for that many SMs' worth of blocks leaves the rest of the GPU to other streams
@@ -1443,7 +1339,7 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
             first = false;
             A.ntiles = (int32_t)std::min<int64_t>(tile, (int64_t)c0 + chunk);
             g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-            HCUDA(cudaLaunchCooperativeKernel((const void *)p->kern, dim3(grid), dim3(threads), args, p->smem, s));
+            HCUDA(cudaLaunchCooperativeKernel((const void *)p->kern, dim3(grid), dim3(threads), args, 0, s));
             if (A.yield) {
                 int32_t handed = 0;  // tiles handed out, all of them finished
                 HCUDA(cudaMemcpyAsync(&handed, p->queue.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1465,9 +1361,9 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
             for (int32_t bi = 0; bi < p->desc[gi].nbatches; ++bi) {
                 const int32_t b = p->desc[gi].b0 + bi * p->desc[gi].bstride;
                 const int32_t s0 = b * 64 * W, ns = std::min(64 * W, p->desc[gi].n - s0);
-                launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
-                launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_START_PUSH, s0, ns, 0, ps, 0);
-                launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, 1, ps, 0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START, s0, ns, 0, ps, 0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_START_PUSH, s0, ns, 0, ps, 0);
+                launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, 1, ps, 0);
                 ++ps;
                 int32_t cur_a = 1;
                 for (int32_t level = 2; level <= p->desc[gi].n + 1; ++level) {
@@ -1476,11 +1372,11 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
                     HCUDA(cudaStreamSynchronize(s));
                     if (h3[0] == 0 || (h3[2] == 0 && !p->jobs[gi].g->directed)) break;
                     if ((unsigned long long)A.push_alpha * h3[1] < h3[2]) {
-                        launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_PUSH, s0, ns, level, ps, cur_a);
-                        launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, level, ps,
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_PUSH, s0, ns, level, ps, cur_a);
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_FINALIZE, s0, ns, level, ps,
                                cur_a);
                     } else {
-                        launch(pkern, grid, threads, p->smem, s, A, (int32_t)gi, (int32_t)PH_PULL, s0, ns, level, ps, cur_a);
+                        launch(pkern, grid, threads, 0, s, A, (int32_t)gi, (int32_t)PH_PULL, s0, ns, level, ps, cur_a);
                     }
                     ++ps;
                     cur_a ^= 1;
