@@ -6,6 +6,8 @@ the same exact integers on both sides, so they are compared bit for bit too
 (stricter than the 1e-12 relative tolerance the path allows; the tolerance is
 used only where stated).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -401,6 +403,81 @@ def test_component_split_directed(H):
     for i in range(len(layers)):
         check_graph(*g.layer_closeness(i), ref.layer(i))
     check_graph(*g.and_closeness(0b11), ref.and_graph(0b11))
+    g.close()
+
+
+def _maximum_size_layer(n, seed):
+    """Edges over the library's largest node count whose components sit on ids spread over the
+    whole range: a 12,000-node BA component, a path of 600 (more levels than the level marks
+    count before wrapping), components at the small-component bound (a path and a cycle of 8, a
+    star of 9), 300 cycles of 12 just above it, 100,000 disjoint pairs; the rest is isolated."""
+    rng = np.random.default_rng(seed)
+    ids = rng.permutation(n).astype(np.int32)
+    parts = []
+    k = 12000
+    s, d = synth.ba_edges(k, 3, seed)
+    parts.append((ids[s], ids[d]))
+    used = k
+    p = 600
+    parts.append((ids[used:used + p - 1], ids[used + 1:used + p]))
+    used += p
+    c = np.arange(8)
+    parts.append((ids[used + c[:-1]], ids[used + c[1:]]))
+    parts.append((ids[used + 8 + c], ids[used + 8 + (c + 1) % 8]))
+    parts.append((np.full(8, ids[used + 16]), ids[used + 17 + c]))
+    used += 25
+    c = np.arange(12)
+    for _ in range(300):
+        parts.append((ids[used + c], ids[used + (c + 1) % 12]))
+        used += 12
+    q = 100000
+    parts.append((ids[used:used + 2 * q:2], ids[used + 1:used + 2 * q:2]))
+    s = np.concatenate([a for a, _ in parts]).astype(np.int32)
+    d = np.concatenate([b for _, b in parts]).astype(np.int32)
+    return s, d
+
+
+def test_maximum_node_count_matches_oracle(H):
+    """n = HOMLN_MAX_NODES (2^20): two layers (the second keeps a seeded 70% of the first's edges
+    and adds 50,000 random ones), so the AND graph has components of its own. Every graph's
+    farness, reach and closeness and the AND edge list against the oracle's full run; the top-10%
+    ground truth, per-layer CC nodes, naive, CC1 and CC2 with their accuracy counts; the exact
+    at-or-above-mean selection with CC2; farness and reach again at 32 words per node."""
+    n = H.MAX_NODES
+    s, d = _maximum_size_layer(n, 71)
+    keep = np.random.default_rng(72).random(s.size) < 0.7
+    extra = np.random.default_rng(73).integers(0, n, size=(2, 50000)).astype(np.int32)
+    layers = [(s, d), (np.concatenate([s[keep], extra[0]]), np.concatenate([d[keep], extra[1]]))]
+    ref = O.OracleHoMLN(n, layers, threads=os.cpu_count() or 1)
+    g = H.Network(n, to_dev(layers))
+    for i in range(2):
+        check_graph(*g.layer_closeness(i), ref.layer(i))
+    gs, gd = g.and_aggregate(3)
+    rs, rd = ref.and_edges(3)
+    assert np.array_equal(gs.cpu().numpy(), rs) and np.array_equal(gd.cpu().numpy(), rd)
+    check_graph(*g.and_closeness(3), ref.and_graph(3))
+    cases = [(H.make_select(H.HOMLN_TOPK_PERCENT, 10.0, cc1_overlap=0.5), O.Select(O.TOPK_PERCENT, 10.0, cc1_overlap=0.5),
+              (0, 1, 2)),
+             (H.make_select(H.HOMLN_GE_MEAN), O.Select(O.GE_MEAN), (2,))]
+    for sel, osel, heuristics in cases:
+        gt = g.topk(-1, 3, sel)
+        want_gt = ref.topk(-1, 3, osel)
+        assert gt.cpu().numpy().tolist() == want_gt.tolist()
+        for i in range(2):
+            assert g.topk(i, 3, sel).cpu().numpy().tolist() == ref.topk(i, 3, osel).tolist()
+        for heur in heuristics:
+            est = g.compose(3, heur, sel)
+            want = ref.compose(3, heur, osel)
+            assert est.cpu().numpy().tolist() == want.tolist(), heur
+            acc = g.accuracy(est, gt)
+            wa = O.accuracy(want, want_gt)
+            assert (acc["tp"], acc["fp"], acc["fn"]) == (wa["tp"], wa["fp"], wa["fn"])
+    g.close()
+    g = H.Network(n, to_dev(layers), tuning=dict(words_per_node=32))
+    for i in range(2):
+        F, R, _ = g.layer_closeness(i)
+        assert np.array_equal(u64(F), ref.layer(i)["F"])
+        assert np.array_equal(R.cpu().numpy().astype(np.uint32), ref.layer(i)["R"])
     g.close()
 
 
