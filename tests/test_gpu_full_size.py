@@ -153,6 +153,56 @@ def test_large_ba_full_size_matches_oracle(H, golden, tuning):
     g.close()
 
 
+def sampled_oracle(n, graphs, outs, count, seed):
+    """Live oracle BFS from a seeded sample of vertices on each (rowptr, col) graph: farness, reach
+    and closeness there against the CUDA path's (F, R, cc)."""
+    sample = np.sort(np.random.default_rng(seed).choice(n, count, replace=False)).astype(np.int32)
+    for (rp, col), (F, R, cc) in zip(graphs, outs):
+        Fs, Rs = O.farness_reach(n, rp, col, sources=sample, threads=os.cpu_count() or 1)
+        assert np.array_equal(F.cpu().numpy().astype(np.uint64)[sample], Fs)
+        assert np.array_equal(R.cpu().numpy().astype(np.uint32)[sample], Rs)
+        assert np.array_equal(cc.cpu().numpy()[sample], O.wf_closeness(n, Fs, Rs))
+
+
+def test_widened_paths_at_full_size_match_sampled_oracle(H, golden):
+    """The benchmark's 4-layer BA network (n = 200,000) through the paths beyond the AND ground
+    truth, at the size the benchmark times them:
+    - OR graphs (edges in at least one layer) of layers {0,1,2,3} and {0,1,2};
+    - the layer-subset sweep (all 11 subsets of two or more layers in one launch): two of its AND
+      graphs against the oracle, and every subset's counts equal to the individual selection,
+      composition and accuracy calls on the sweep's results;
+    - the directed variant (each edge a random-direction arc, plus the reverse of 25% of them):
+      in-closeness of the 4 layers and of their AND graph.
+    Farness, reach and closeness at 1,000 seeded vertices per graph against live oracle BFS."""
+    net = synth.homln_ba_large()
+    check_inputs(net, golden["ba200k"])
+    n, L = net.n, net.n_layers
+    keys = [O.edge_keys(n, a, b) for a, b in net.layers]
+    g = H.Network(n, to_dev(net.layers))
+    sel = H.make_select(H.HOMLN_TOPK_PERCENT, 10.0)
+    res = H.homln_subset_sweep(g.h, H.HOMLN_CC2, sel, 2)
+    assert [r["mask"] for r in res] == [m for m in range(1, 16) if bin(m).count("1") >= 2]
+    masks = (3, 10)
+    sampled_oracle(n, [O.csr_from_keys(n, O.and_keys(n, [keys[i] for i in range(L) if m >> i & 1])) for m in masks],
+                   [g.and_closeness(m) for m in masks], 1000, 5101)
+    for r in res:
+        gt = g.topk(-1, r["mask"], sel)
+        est = g.compose(r["mask"], H.HOMLN_CC2, sel)
+        acc = g.accuracy(est, gt)
+        assert (r["truth_count"], r["estimate_count"]) == (gt.shape[0], est.shape[0])
+        assert (r["tp"], r["fp"], r["fn"]) == (acc["tp"], acc["fp"], acc["fn"])
+    or_masks = (15, 7)
+    sampled_oracle(n, [O.csr_from_keys(n, O.or_keys(n, [keys[i] for i in range(L) if m >> i & 1])) for m in or_masks],
+                   [g.or_closeness(m) for m in or_masks], 1000, 5102)
+    g.close()
+    arcs = [synth.with_reciprocal(e, 0.25, 7001 + i) for i, e in enumerate(net.layers)]
+    gd = H.Network(n, to_dev(arcs), directed=True)
+    akeys = [O.arc_keys(n, a, b) for a, b in arcs]
+    graphs = [O.arc_csr(n, k, reverse=True) for k in akeys] + [O.arc_csr(n, O.and_keys(n, akeys), reverse=True)]
+    sampled_oracle(n, graphs, [gd.layer_closeness(i) for i in range(L)] + [gd.and_closeness((1 << L) - 1)], 1000, 5103)
+    gd.close()
+
+
 def test_batch_config_full_size_matches_oracle(H, golden):
     """64 HoMLNs (2-8 ER/BA layers, 500-20,000 nodes) in one persistent launch with several teams: every
     graph's farness/reach/closeness and every network's top-10% ground truth, per-layer CC nodes,
