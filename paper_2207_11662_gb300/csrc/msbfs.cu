@@ -293,6 +293,21 @@ __device__ __forceinline__ bool team_sync(const TeamBarrier &b) {
 #endif
 constexpr int kUnroll = HOMLN_GATHER_UNROLL;
 
+// Leaves of undirected graphs are folded out of the BFS. A vertex v whose only neighbour p has
+// other neighbours is one hop further than p from every other source, so over all sources
+// F(v) = F(p) + R(p) - 1 and R(v) = R(p). Such a vertex is quiet from the start of every batch
+// (never swept, gathered for or pushed to); its own source bit still reaches p on level 1, which
+// pushes every source's bit to its neighbours. k_fold_leaves fills in F(v) and R(v) afterwards.
+#ifndef HOMLN_FOLD_LEAVES
+#define HOMLN_FOLD_LEAVES 1
+#endif
+__host__ __device__ __forceinline__ bool folded_leaf(const int64_t *rowptr, const int32_t *col, int64_t v) {
+    const int64_t r = rowptr[v];
+    if (rowptr[v + 1] - r != 1) return false;
+    const int64_t p = col[r];
+    return rowptr[p + 1] - rowptr[p] >= 2;
+}
+
 #ifndef HOMLN_DEBUG
 #define HOMLN_DEBUG 0
 #endif
@@ -522,7 +537,8 @@ __device__ void phase_start_batch(const Tile &a, uint64_t *s0buf, uint64_t *s1bu
         }
         if (wi0 == 0) {
             const bool lonely = c1 - c0 - (source ? 1 : 0) <= 0 || a.prow[v + 1] == a.prow[v];
-            a.quiet[v] = lonely ? QUIET : 0;
+            const bool leaf = HOMLN_FOLD_LEAVES && a.prow == a.rowptr && folded_leaf(a.prow, a.pcol, v);
+            a.quiet[v] = lonely || leaf ? QUIET : 0;
             a.fresh[v] = 0;
             a.pushed[v] = 0;
         }
@@ -1095,6 +1111,25 @@ PhaseKernel phase_kernel_for(int W, bool stats) {
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
+// Farness and reach of the folded leaves (see folded_leaf), from their neighbour's. A shard (source
+// batches b0, b0 + bstride, ... of spb sources) holds partial sums over its own sources S, and the
+// sums over shards must add up: over S, F_S(v) = F_S(p) + R_S(p) + [p in S] - 2 [v in S] and
+// R_S(v) = R_S(p) + [p in S] - [v in S] (with one shard of everything: F(p) + R(p) - 1, R(p)).
+__global__ void k_fold_leaves(int32_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              uint64_t *F, uint32_t *R, int32_t spb, int32_t b0, int32_t bstride) {
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (!folded_leaf(rowptr, col, v)) continue;
+        const int32_t p = col[rowptr[v]];
+        auto in_shard = [&](int32_t x) {
+            const int32_t b = x / spb;
+            return b >= b0 && (b - b0) % bstride == 0 ? 1u : 0u;
+        };
+        const uint32_t ip = in_shard(p), iv = in_shard(v);
+        F[v] = F[p] + R[p] + ip - 2ull * iv;
+        R[v] = R[p] + ip - iv;
+    }
+}
+
 __global__ void k_scatter_back(int32_t n, const int32_t *__restrict__ perm, const uint64_t *__restrict__ Fi,
                                const uint32_t *__restrict__ Ri, uint64_t *__restrict__ F, uint32_t *__restrict__ R) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1385,6 +1420,13 @@ void bfs_plan_run(BfsPlan *p, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t 
         }
     }
     if (ev_stop) HCUDA(cudaEventRecord(ev_stop, s));
+    if (HOMLN_FOLD_LEAVES)
+        for (size_t i = 0; i < ng; ++i) {
+            const GraphDesc &d = p->desc[i];
+            if (d.prow == d.rowptr && d.n > 0)
+                launch(k_fold_leaves, (unsigned)std::min<int64_t>(ceil_div(d.n, 256), 4096), 256, 0, s, d.n, d.prow,
+                       d.pcol, d.F, d.R, 64 * W, d.b0, d.bstride);
+        }
     for (size_t i = 0; i < ng; ++i)
         if (p->jobs[i].g->relabeled)
             launch(k_scatter_back, (unsigned)ceil_div(p->desc[i].n, 256), 256, 0, s, p->desc[i].n,
