@@ -165,8 +165,8 @@ def sampled_oracle(n, graphs, outs, count, seed):
 
 
 def test_widened_paths_at_full_size_match_sampled_oracle(H, golden):
-    """The benchmark's 4-layer BA network (n = 200,000) through the paths beyond the AND ground
-    truth, at the size the benchmark times them:
+    """The benchmark's largest network (4 BA layers, n = 200,000; the benchmark times these paths on
+    the 50,000-node power-law network) through the paths beyond the AND ground truth:
     - OR graphs (edges in at least one layer) of layers {0,1,2,3} and {0,1,2};
     - the layer-subset sweep (all 11 subsets of two or more layers in one launch): two of its AND
       graphs against the oracle, and every subset's counts equal to the individual selection,
