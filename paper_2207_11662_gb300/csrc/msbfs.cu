@@ -116,12 +116,14 @@ struct Tile {
 
 // Two snapshots per team: level l reads snapshot (l-1) mod 2 and writes snapshot l mod 2.
 // Invariant: after level l, snapshot l mod 2 holds state_l(v) -- the sources within distance
-// l of v -- for every vertex. A vertex rewrites its words of the next snapshot only if it
-// finds new bits at level l, or found some at level l-1 (then the next snapshot still holds
-// state_{l-2}, which differs); otherwise they already hold state_{l-2} = state_{l-1} =
-// state_l. fresh[v] marks the last level at which v found new bits. A vertex is "quiet" once
-// both snapshots hold every bit (one level after its words became full): every later level
-// of the batch skips it after reading one byte, and nobody pushes to it.
+// l of v -- for every vertex but the folded leaves (folded_leaf), whose words keep the start
+// state: only their one neighbour reads them, and it has their bits from level 1. A vertex
+// rewrites its words of the next snapshot only if it finds new bits at level l, or found some
+// at level l-1 (then the next snapshot still holds state_{l-2}, which differs); otherwise they
+// already hold state_{l-2} = state_{l-1} = state_l. fresh[v] marks the last level at which v
+// found new bits. A vertex is "quiet" once both snapshots hold every bit (one level after its
+// words became full): every later level of the batch skips it after reading one byte, and
+// nobody pushes to it.
 constexpr uint8_t QUIET = 1;  // quiet byte of a full vertex
 
 __device__ __forceinline__ uint8_t level_mark(int level) { return (uint8_t)(1 + level % 255); }
